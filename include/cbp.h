@@ -1,0 +1,135 @@
+/* libcbp: check-belief propagation (CBP) decoding of QC-LDPC codes on sm_103a.
+ *
+ * Method: W. Guan and L. Liang, "Check-Belief Propagation Decoding of LDPC Codes",
+ * Sec. IV.  Each check-node keeps a check-belief Omega_c (Eq. s4e1); in the
+ * sequential order of the check-nodes, every edge (c_i, v) runs
+ *   B2V  R^new_{c_j->v} = psi^-(Omega_{c_j}, Q_{v->c*})            Eq. (s4e18)
+ *   V2C  Q^new = Q + R^new - R_{c_i->v},  Lambda = Q + R^new        Eqs. (s4e19), (s4e20)
+ *   C2B  Omega_{c_i} <- psi^+(Omega_{c_i}, Q^new)                    Eq. (s4e21)
+ * where c_j is the check that updated v last (Step 2 a).  Hard decisions follow
+ * Eq. (s2e7); decoding of a frame stops after the first full sweep whose hard
+ * decisions satisfy every parity check (syndrome stop).
+ *
+ * Code model (Sec. II): a quasi-cyclic parity-check matrix given by a base matrix
+ * B (mb x nb, row-major, -1 = zero block, s in [0, Z) = identity shifted by s) and
+ * the lifting Z:  H[r*Z + i][c*Z + (i + s) % Z] = 1.  N = nb*Z variables, M = mb*Z
+ * checks, checks visited in ascending index r*Z + i, the variables of a check in
+ * ascending base column.
+ *
+ * Numerics.  All algorithms compute in FP32 with a fixed operation order (no
+ * contraction into fused multiply-adds outside phi).  phi(x) = -log tanh(x/2)
+ * (Eq. s2e5) is evaluated as phi(clamp(x, phi(30), 30)) by a cubic Taylor
+ * expansion around the nearest point of a fixed grid (32 points per binade below
+ * 2, step 1/16 from 2 to 30), coefficients from the closed-form derivatives of phi.
+ * The check-belief is stored as S_c = sum of phi(|Q|) with its sign (Appendix A,
+ * Eqs. ae2-ae5).  A variable seen for the first time adds no C2V message; the C2V
+ * store of Eq. (s4e22) writes the predecessor's slot R_{c_j->v}.
+ *
+ * Threading and streams.  Every call is asynchronous on the stream it is given and
+ * may run concurrently with other calls that use distinct output and workspace
+ * buffers.  A code handle belongs to the device that was current at creation.
+ *
+ * Errors.  Functions return CBP_OK (0) or a negative cbp_status.  Arguments are
+ * checked on the host before anything is launched; a failed check launches
+ * nothing and leaves the outputs untouched.  Device data (LLR values) is not
+ * inspected: LLRs must be finite.
+ */
+#ifndef CBP_H
+#define CBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque decoder description of one QC code on one device; immutable after creation. */
+typedef struct cbp_code cbp_code_t;
+
+/* A CUDA stream (cudaStream_t); NULL is the legacy default stream. */
+typedef struct CUstream_st* cbp_stream_t;
+
+typedef enum cbp_status {
+  CBP_OK = 0,
+  CBP_EINVAL = -1,        /* bad argument: null/misaligned pointer, size, shift, option */
+  CBP_ENOMEM = -2,        /* device allocation failed (only cbp_code_create allocates) */
+  CBP_ECUDA = -3,         /* a CUDA runtime call or a kernel launch failed */
+  CBP_EUNSUPPORTED = -4,  /* valid code/option this build cannot run (e.g. Z > 1024) */
+  CBP_EWORKSPACE = -5,    /* workspace smaller than cbp_workspace_bytes() */
+  CBP_EDEVICE = -6        /* handle used on a device other than the one it was made on */
+} cbp_status;
+
+/* Decoding algorithm.  All share the check order, the hard decision and the stop. */
+typedef enum cbp_alg {
+  CBP_ALG_CBP_SP = 0,   /* CBP, log-tanh form (Sec. IV-C, Steps 1-3) */
+  CBP_ALG_CBP_NMS = 1,  /* CBP normalized min-sum, Eqs. (s4e18xx), (s4e21xx) */
+  CBP_ALG_LBP_NMS = 2,  /* layered normalized min-sum, Eqs. (s2e10), (s2e12) (comparator) */
+  CBP_ALG_FBP_SP = 3    /* flooding sum-product BP, Eqs. (s3e1), (s3e2), (s2e6) (comparator) */
+} cbp_alg;
+
+typedef enum cbp_stop {
+  CBP_STOP_SYNDROME = 0, /* stop a frame after the first sweep with H x^T = 0 */
+  CBP_STOP_NONE = 1      /* always run max_iter sweeps */
+} cbp_stop;
+
+/* Options of cbp_decode_ex.  Zero-initialise, then set what you need;
+ * alpha <= 0 means the default 0.75. */
+typedef struct cbp_opts {
+  int alg;          /* cbp_alg */
+  float alpha;      /* min-sum normalisation (CBP_NMS, LBP_NMS); ignored otherwise */
+  int stop_mode;    /* cbp_stop */
+  float* soft_out;  /* optional device buffer [batch][N] fp32: the posterior LLR
+                       (CBP: Eq. s4e20 evaluated at the end of the last sweep run) */
+} cbp_opts_t;
+
+/* Build a code handle from a host base matrix (row-major mb x nb, int32, -1 = zero
+ * block, otherwise a shift in [0, Z)).  Every base row needs >= 2 entries and every
+ * base column >= 1 (CBP_EINVAL otherwise).  Z <= 1024, mb, nb <= 4096 and at most
+ * 65535 base entries (CBP_EUNSUPPORTED otherwise).  Allocates the device tables on
+ * the current device; *out is set only on success.  Release with cbp_code_destroy. */
+int cbp_code_create(const int32_t* base, int mb, int nb, int Z, cbp_code_t** out);
+
+/* Release a handle and its device tables (NULL is ignored).  The caller makes sure
+ * no decode using it is still running. */
+void cbp_code_destroy(cbp_code_t* code);
+
+/* Sizes: n = N, m = M, k = N - rank(H) if known (-1 if not computed), edges = E.
+ * Any output pointer may be NULL. */
+int cbp_code_info(const cbp_code_t* code, int* n, int* m, int* k, int* edges);
+
+/* Bytes of device workspace a decode of `batch` frames with `opts` (NULL = defaults)
+ * needs.  The workspace holds the per-frame-slot C2V messages; it is scratch
+ * memory, its contents need no initialisation and are undefined afterwards. */
+int cbp_workspace_bytes(const cbp_code_t* code, int batch, const cbp_opts_t* opts,
+                        size_t* bytes);
+
+/* Decode `batch` frames with CBP (log-tanh form) and the syndrome stop.
+ *   llr        device, [batch][N] fp32 channel LLRs ln Pr(y|0)/Pr(y|1), 16-byte aligned
+ *   hard_out   device, [batch][ceil(N/32)] uint32: bit (v % 32) of word v / 32 is x_v
+ *   iters_out  device, [batch] int32: sweeps run, negated if the syndrome is non-zero
+ *              after max_iter sweeps
+ *   max_iter   >= 1 sweeps at most;  batch >= 0 (0 launches nothing)
+ *   workspace  device, >= cbp_workspace_bytes(), 256-byte aligned, caller-owned
+ * Asynchronous on `stream`; the library allocates nothing. */
+int cbp_decode(const cbp_code_t* code, const float* llr, uint32_t* hard_out,
+               int32_t* iters_out, int max_iter, int batch, void* workspace,
+               size_t workspace_bytes, cbp_stream_t stream);
+
+/* cbp_decode with an algorithm, stop mode and optional soft output (opts may be NULL). */
+int cbp_decode_ex(const cbp_code_t* code, const float* llr, uint32_t* hard_out,
+                  int32_t* iters_out, int max_iter, int batch, void* workspace,
+                  size_t workspace_bytes, cbp_stream_t stream, const cbp_opts_t* opts);
+
+/* Evaluate the library's phi (Eq. s2e5, the clamped FP32 form used by the decoders)
+ * on n device values: y[i] = phi(x[i]).  x, y device, 4-byte aligned, n >= 0. */
+int cbp_phi(const float* x, float* y, int64_t n, cbp_stream_t stream);
+
+/* Static description of an error code. */
+const char* cbp_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CBP_H */

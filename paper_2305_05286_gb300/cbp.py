@@ -1,0 +1,198 @@
+"""Thin Python binding of libcbp (include/cbp.h): argument marshalling only.
+
+Every decoding step runs in the CUDA kernels of libcbp.so; this module passes
+torch device pointers and the current stream through ctypes.  There is no CPU
+fallback: without the built library, or without a CUDA device, calls raise.
+
+    from paper_2305_05286_gb300 import cbp, inputs
+    code = cbp.Code.from_qc(inputs.code_576())
+    hard, iters, soft = code.decode(llr_cuda, max_iter=30, alg="cbp_sp", soft=True)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+
+import torch
+
+from . import build as _build
+
+ALGS = {"cbp_sp": 0, "cbp_nms": 1, "lbp_nms": 2, "fbp_sp": 3}
+STOPS = {"syndrome": 0, "none": 1}
+STATUS = {0: "CBP_OK", -1: "CBP_EINVAL", -2: "CBP_ENOMEM", -3: "CBP_ECUDA",
+          -4: "CBP_EUNSUPPORTED", -5: "CBP_EWORKSPACE", -6: "CBP_EDEVICE"}
+
+# Every symbol include/cbp.h declares (checked by the ABI test).
+EXPORTS = ("cbp_code_create", "cbp_code_destroy", "cbp_code_info", "cbp_workspace_bytes",
+           "cbp_decode", "cbp_decode_ex", "cbp_phi", "cbp_strerror")
+
+
+class CbpError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        msg = lib().cbp_strerror(status).decode()
+        super().__init__(f"{fn} failed: {STATUS.get(status, status)} ({msg})")
+
+
+class _Opts(C.Structure):
+    _fields_ = [("alg", C.c_int), ("alpha", C.c_float), ("stop_mode", C.c_int),
+                ("soft_out", C.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib(build_if_needed: bool = True):
+    """Load libcbp.so from the package's _build directory (building it if stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_needed else _build.LIB
+            L = C.CDLL(path)
+            P, I, Z = C.c_void_p, C.c_int, C.c_size_t
+            L.cbp_code_create.restype = I
+            L.cbp_code_create.argtypes = [P, I, I, I, C.POINTER(C.c_void_p)]
+            L.cbp_code_destroy.restype = None
+            L.cbp_code_destroy.argtypes = [P]
+            L.cbp_code_info.restype = I
+            L.cbp_code_info.argtypes = [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]
+            L.cbp_workspace_bytes.restype = I
+            L.cbp_workspace_bytes.argtypes = [P, I, C.POINTER(_Opts), C.POINTER(Z)]
+            L.cbp_decode.restype = I
+            L.cbp_decode.argtypes = [P, P, P, P, I, I, P, Z, P]
+            L.cbp_decode_ex.restype = I
+            L.cbp_decode_ex.argtypes = [P, P, P, P, I, I, P, Z, P, C.POINTER(_Opts)]
+            L.cbp_phi.restype = I
+            L.cbp_phi.argtypes = [P, P, C.c_int64, P]
+            L.cbp_strerror.restype = C.c_char_p
+            L.cbp_strerror.argtypes = [I]
+            _lib = L
+    return _lib
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _check(fn: str, rc: int):
+    if rc != 0:
+        raise CbpError(fn, rc)
+
+
+def _opts(alg: str, alpha: float, stop: str, soft_ptr: int | None) -> _Opts:
+    return _Opts(ALGS[alg], float(alpha), STOPS[stop], soft_ptr or None)
+
+
+class Code:
+    """A QC-LDPC code on the current CUDA device (cbp_code_create)."""
+
+    def __init__(self, base, Z: int):
+        import numpy as np
+
+        b = np.ascontiguousarray(np.asarray(base, dtype=np.int32))
+        if b.ndim != 2:
+            raise ValueError("base matrix must be 2-D")
+        self.base = b
+        self.Z = int(Z)
+        self.device = torch.cuda.current_device()
+        h = C.c_void_p()
+        _check("cbp_code_create",
+               lib().cbp_code_create(b.ctypes.data, b.shape[0], b.shape[1], self.Z, C.byref(h)))
+        self._h = h
+        n, m, k, e = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check("cbp_code_info", lib().cbp_code_info(h, C.byref(n), C.byref(m), C.byref(k), C.byref(e)))
+        self.N, self.M, self.K, self.E = n.value, m.value, k.value, e.value
+        self.words = (self.N + 31) // 32
+        self._ws = None
+
+    @classmethod
+    def from_qc(cls, qc) -> "Code":
+        return cls(qc.base, qc.Z)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.cbp_code_destroy(h)
+            self._h = None
+
+    # ------------------------------------------------------------------ workspace
+    def workspace_bytes(self, batch: int, alg: str = "cbp_sp") -> int:
+        nb = C.c_size_t()
+        o = _opts(alg, 0.75, "syndrome", None)
+        _check("cbp_workspace_bytes", lib().cbp_workspace_bytes(self._h, int(batch), C.byref(o), C.byref(nb)))
+        return nb.value
+
+    def workspace(self, batch: int, alg: str = "cbp_sp") -> torch.Tensor:
+        """A cached device workspace big enough for (batch, alg)."""
+        need = self.workspace_bytes(batch, alg)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=f"cuda:{self.device}")
+        return self._ws
+
+    # ------------------------------------------------------------------ decode
+    def decode_into(self, llr: torch.Tensor, hard: torch.Tensor, iters: torch.Tensor,
+                    max_iter: int = 30, alg: str = "cbp_sp", alpha: float = 0.75,
+                    stop: str = "syndrome", soft: torch.Tensor | None = None,
+                    workspace: torch.Tensor | None = None, stream=None) -> None:
+        """cbp_decode_ex on caller-provided device tensors (no allocation)."""
+        B = llr.shape[0]
+        if llr.dtype != torch.float32 or not llr.is_cuda or not llr.is_contiguous():
+            raise ValueError("llr must be a contiguous float32 CUDA tensor")
+        if llr.numel() != B * self.N:
+            raise ValueError(f"llr must have {self.N} values per frame")
+        if hard.numel() < B * self.words or iters.numel() < B:
+            raise ValueError("output tensors too small")
+        ws = workspace if workspace is not None else self.workspace(B, alg)
+        o = _opts(alg, alpha, stop, soft.data_ptr() if soft is not None else None)
+        rc = lib().cbp_decode_ex(self._h, llr.data_ptr(), hard.data_ptr(), iters.data_ptr(),
+                                 int(max_iter), int(B), ws.data_ptr(), ws.numel(),
+                                 _stream_ptr(stream), C.byref(o))
+        _check("cbp_decode_ex", rc)
+
+    def decode(self, llr: torch.Tensor, max_iter: int = 30, alg: str = "cbp_sp",
+               alpha: float = 0.75, stop: str = "syndrome", soft: bool = False, stream=None):
+        """Decode [B, N] LLRs.  Returns (hard int32 [B, ceil(N/32)] bit words,
+        iters int32 [B], soft float32 [B, N] or None).
+
+        A CPU ``llr`` is copied to the device first and the results are copied back
+        (the end-to-end path); a CUDA ``llr`` stays on the device."""
+        host = not llr.is_cuda
+        dev = torch.device(f"cuda:{self.device}")
+        x = llr.to(dev, non_blocking=True) if host else llr
+        x = x.contiguous()
+        B = x.shape[0]
+        hard = torch.empty((B, self.words), dtype=torch.int32, device=dev)
+        iters = torch.empty((B,), dtype=torch.int32, device=dev)
+        sb = torch.empty((B, self.N), dtype=torch.float32, device=dev) if soft else None
+        self.decode_into(x, hard, iters, max_iter, alg, alpha, stop, sb, stream=stream)
+        if host:
+            pin = llr.is_pinned()
+            hard_h = torch.empty(hard.shape, dtype=hard.dtype, pin_memory=pin)
+            iters_h = torch.empty(iters.shape, dtype=iters.dtype, pin_memory=pin)
+            hard_h.copy_(hard, non_blocking=pin)
+            iters_h.copy_(iters, non_blocking=pin)
+            sb_h = sb.cpu() if sb is not None else None
+            if pin:
+                torch.cuda.current_stream(dev).synchronize()
+            return hard_h, iters_h, sb_h
+        return hard, iters, sb
+
+
+def phi(x: torch.Tensor, stream=None) -> torch.Tensor:
+    """The library's FP32 phi (Eq. s2e5) applied elementwise on the device (cbp_phi)."""
+    if x.dtype != torch.float32 or not x.is_cuda:
+        raise ValueError("x must be a float32 CUDA tensor")
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    _check("cbp_phi", lib().cbp_phi(x.data_ptr(), y.data_ptr(), x.numel(), _stream_ptr(stream)))
+    return y
+
+
+def unpack_bits(words: torch.Tensor, N: int) -> torch.Tensor:
+    """[B, ceil(N/32)] int32 bit words -> [B, N] uint8 hard decisions (bit v%32 of word v/32)."""
+    w = words.to(torch.int64) & 0xFFFFFFFF
+    shifts = torch.arange(32, device=w.device, dtype=torch.int64)
+    b = (w[:, :, None] >> shifts) & 1
+    return b.reshape(w.shape[0], -1)[:, :N].to(torch.uint8)

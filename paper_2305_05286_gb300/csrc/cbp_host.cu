@@ -1,0 +1,530 @@
+// libcbp host side: the C ABI of include/cbp.h, code tables, phi table, launch planning.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "cbp_internal.cuh"
+
+namespace cbp {
+
+// ---------------------------------------------------------------------------
+// phi coefficient table.  For every grid centre m with normalisation h the cubic
+// Taylor coefficients phi^(k)(m) h^k / k! are computed in FP64 from
+//   phi(m) = log1p(2 / expm1(m)),  phi'(m) = -1/sinh m,  phi''(m) = cosh m / sinh^2 m,
+//   phi'''(m) = -(1 + cosh^2 m) / sinh^3 m,
+// and rounded to FP32.
+// ---------------------------------------------------------------------------
+void phi_table_host(float* coef, float* xlo) {
+  for (int i = 0; i < kPhiSegments; ++i) {
+    double m, h;
+    if (i < kPhiLogCount) {
+      uint32_t u = static_cast<uint32_t>(kPhiLogBase + i) << 18;
+      float mf;
+      std::memcpy(&mf, &u, sizeof mf);
+      m = mf;
+      int ex;
+      std::frexp(m, &ex);      // m = f * 2^ex, f in [0.5, 1)
+      h = std::ldexp(1.0, ex - 1);
+    } else {
+      m = static_cast<double>(i - kPhiLogCount + 32) / 16.0;
+      h = 0.0625;
+    }
+    const double a = h / std::sinh(m);
+    const double co = std::cosh(m);
+    coef[4 * i + 0] = static_cast<float>(std::log1p(2.0 / std::expm1(m)));
+    coef[4 * i + 1] = static_cast<float>(-a);
+    coef[4 * i + 2] = static_cast<float>(0.5 * co * (a * a));
+    coef[4 * i + 3] = static_cast<float>(-(co * co + 1.0) * (a * a * a) / 6.0);
+  }
+  *xlo = static_cast<float>(std::log1p(2.0 / std::expm1(30.0)));
+}
+
+__device__ float4 g_phi_tab[kPhiSegments];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+struct DeviceInfo {
+  bool ready = false;
+  int sms = 0;
+  int smem_optin = 0;
+  float4* tab = nullptr;  // device address of g_phi_tab on this device
+  float xlo = 0.0f;
+};
+
+std::mutex g_mu;
+DeviceInfo g_dev[kMaxDevices];
+
+int device_init(int dev, DeviceInfo** out) {
+  if (dev < 0 || dev >= kMaxDevices) return CBP_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lk(g_mu);
+  DeviceInfo& d = g_dev[dev];
+  if (!d.ready) {
+    static std::vector<float> coef;
+    static float xlo = 0.0f;
+    if (coef.empty()) {
+      coef.resize(4 * kPhiSegments);
+      phi_table_host(coef.data(), &xlo);
+    }
+    if (cudaMemcpyToSymbol(g_phi_tab, coef.data(), sizeof(float) * coef.size()) != cudaSuccess)
+      return CBP_ECUDA;
+    void* addr = nullptr;
+    if (cudaGetSymbolAddress(&addr, g_phi_tab) != cudaSuccess) return CBP_ECUDA;
+    if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess)
+      return CBP_ECUDA;
+    const Variant all[] = {{ALG_CBP_SP, true, true},  {ALG_CBP_SP, true, false},
+                           {ALG_CBP_SP, false, true}, {ALG_CBP_SP, false, false},
+                           {ALG_CBP_NMS, false, true}, {ALG_CBP_NMS, false, false},
+                           {ALG_LBP_NMS, false, true}, {ALG_FBP_SP, false, false}};
+    for (const Variant& v : all)
+      if (decoder_set_smem(v, d.smem_optin) != cudaSuccess) return CBP_ECUDA;
+    d.tab = static_cast<float4*>(addr);
+    d.xlo = xlo;
+    d.ready = true;
+  }
+  *out = &d;
+  return CBP_OK;
+}
+
+int current_device(DeviceInfo** out, int* dev_out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CBP_ECUDA;
+  if (dev_out) *dev_out = dev;
+  return device_init(dev, out);
+}
+
+}  // namespace
+
+size_t shared_fixed_bytes(const Variant& v, int nnzb, int mb, int nb, int F) {
+  size_t b = 0;
+  if (v.alg == ALG_CBP_SP || v.alg == ALG_FBP_SP) b += sizeof(float4) * kPhiSegments;
+  b += sizeof(BaseEdge) * nnzb;
+  b += sizeof(int) * ((mb + 1 + 3) & ~3);
+  if (v.alg == ALG_FBP_SP) {
+    b += sizeof(ColEntry) * ((nnzb + 1) & ~1);
+    b += sizeof(int) * ((nb + 1 + 3) & ~3);
+  } else {
+    b += sizeof(uint32_t) * ((nb + 3) & ~3);
+  }
+  b += 12 * ((F + 3) & ~3);
+  return b;
+}
+
+size_t shared_frame_floats(const Variant& v, int N, int M, int words) {
+  const size_t Np = (N + 3) & ~3, Mp = (M + 3) & ~3, Wp = (words + 3) & ~3;
+  size_t f = Np + Wp;
+  if (v.alg == ALG_CBP_SP && v.phi_cache) f += Np;
+  if (v.chk_shared) {
+    if (v.alg == ALG_CBP_SP) f += Mp;
+    if (v.alg == ALG_CBP_NMS) f += 2 * Mp;
+  }
+  return f;
+}
+
+size_t ws_slot_floats(const Variant& v, int N, int M, int E) {
+  (void)N;
+  size_t f = E;
+  if (!v.chk_shared) {
+    if (v.alg == ALG_CBP_SP) f += M;
+    if (v.alg == ALG_CBP_NMS) f += 2 * static_cast<size_t>(M);
+  }
+  return (f + 63) & ~static_cast<size_t>(63);  // 256-byte aligned slots
+}
+
+}  // namespace cbp
+
+using namespace cbp;
+
+struct cbp_code {
+  int dev = 0;
+  int mb = 0, nb = 0, Z = 0, N = 0, M = 0, E = 0, K = -1, nnzb = 0, maxdeg = 0;
+  CodeDev d;
+};
+
+namespace {
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// GF(2) rank of a small dense H (bit-packed rows).
+int gf2_rank(const int32_t* base, int mb, int nb, int Z) {
+  const int N = nb * Z, M = mb * Z, W = (N + 63) / 64;
+  std::vector<uint64_t> h(static_cast<size_t>(M) * W, 0);
+  for (int r = 0; r < mb; ++r)
+    for (int i = 0; i < Z; ++i)
+      for (int c = 0; c < nb; ++c) {
+        int s = base[r * nb + c];
+        if (s < 0) continue;
+        int v = c * Z + (i + s) % Z;
+        h[static_cast<size_t>(r * Z + i) * W + v / 64] ^= uint64_t(1) << (v % 64);
+      }
+  int rank = 0;
+  for (int col = 0; col < N && rank < M; ++col) {
+    const int w = col / 64;
+    const uint64_t bit = uint64_t(1) << (col % 64);
+    int piv = -1;
+    for (int r = rank; r < M; ++r)
+      if (h[static_cast<size_t>(r) * W + w] & bit) {
+        piv = r;
+        break;
+      }
+    if (piv < 0) continue;
+    if (piv != rank)
+      for (int k = 0; k < W; ++k)
+        std::swap(h[static_cast<size_t>(piv) * W + k], h[static_cast<size_t>(rank) * W + k]);
+    for (int r = 0; r < M; ++r)
+      if (r != rank && (h[static_cast<size_t>(r) * W + w] & bit))
+        for (int k = 0; k < W; ++k)
+          h[static_cast<size_t>(r) * W + k] ^= h[static_cast<size_t>(rank) * W + k];
+    ++rank;
+  }
+  return rank;
+}
+
+struct Plan {
+  Variant v;
+  int F = 0, threads = 0, grid = 0;
+  size_t smem = 0;
+  long long ws_slot = 0;
+  int sh_frame = 0;
+  size_t ws_bytes = 0;
+};
+
+int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan* out) {
+  std::vector<Variant> cands;
+  switch (alg) {
+    case ALG_CBP_SP:
+      cands = {{ALG_CBP_SP, true, true}, {ALG_CBP_SP, false, true}, {ALG_CBP_SP, false, false}};
+      break;
+    case ALG_CBP_NMS:
+      cands = {{ALG_CBP_NMS, false, true}, {ALG_CBP_NMS, false, false}};
+      break;
+    case ALG_LBP_NMS:
+      if (c->maxdeg > kMaxDeg) return CBP_EUNSUPPORTED;
+      cands = {{ALG_LBP_NMS, false, true}};
+      break;
+    case ALG_FBP_SP:
+      if (c->maxdeg > kMaxDeg) return CBP_EUNSUPPORTED;
+      cands = {{ALG_FBP_SP, false, false}};
+      break;
+    default:
+      return CBP_EINVAL;
+  }
+  const int words = (c->N + 31) / 32;
+  bool found = false;
+  Plan best;
+  int best_warps = -1;
+  for (const Variant& v : cands) {
+    cudaFuncAttributes fa;
+    if (decoder_func_attrs(v, &fa) != cudaSuccess) return CBP_ECUDA;
+    const int fmax = fa.maxThreadsPerBlock / c->Z;
+    if (fmax < 1) continue;
+    const size_t fr_floats = shared_frame_floats(v, c->N, c->M, words);
+    Plan pv;
+    int pv_warps = -1;
+    for (int F = 1; F <= fmax; ++F) {
+      const size_t smem = shared_fixed_bytes(v, c->nnzb, c->mb, c->nb, F) + F * fr_floats * 4;
+      if (smem > static_cast<size_t>(di.smem_optin)) break;
+      const int threads = (F * c->Z + 31) / 32 * 32;
+      if (threads > fa.maxThreadsPerBlock) break;
+      int ctas = 0;
+      if (decoder_occupancy(v, threads, smem, &ctas) != cudaSuccess) return CBP_ECUDA;
+      const int warps = ctas * threads / 32;
+      if (ctas >= 1 && warps >= pv_warps) {
+        pv_warps = warps;
+        pv.v = v;
+        pv.F = F;
+        pv.threads = threads;
+        pv.smem = smem;
+        pv.sh_frame = static_cast<int>(fr_floats);
+        pv.grid = ctas;  // CTAs per SM for now
+      }
+    }
+    if (pv_warps < 0) continue;
+    // first feasible candidate with at least 8 resident warps per SM wins
+    if (!found || (best_warps < 8 && pv_warps > best_warps)) {
+      best = pv;
+      best_warps = pv_warps;
+      found = true;
+    }
+    if (best_warps >= 8) break;
+  }
+  if (!found) return CBP_EUNSUPPORTED;
+  const int ctas_per_sm = best.grid;
+  // small batches: fewer frames per CTA so the frames spread over the SMs
+  const int spread = std::max(1, (batch + di.sms - 1) / di.sms);
+  if (best.F > spread) {
+    best.F = spread;
+    best.threads = (best.F * c->Z + 31) / 32 * 32;
+    best.smem = shared_fixed_bytes(best.v, c->nnzb, c->mb, c->nb, best.F) +
+                best.F * static_cast<size_t>(best.sh_frame) * 4;
+  }
+  const long long need = (static_cast<long long>(batch) + best.F - 1) / best.F;
+  best.grid = static_cast<int>(std::max(1LL, std::min<long long>(need, 1LL * di.sms * ctas_per_sm)));
+  best.ws_slot = static_cast<long long>(ws_slot_floats(best.v, c->N, c->M, c->E));
+  best.ws_bytes = static_cast<size_t>(best.grid) * best.F * best.ws_slot * sizeof(float);
+  *out = best;
+  return CBP_OK;
+}
+
+int check_opts(const cbp_opts_t* o, int* alg, float* alpha, int* stop, float** soft) {
+  *alg = CBP_ALG_CBP_SP;
+  *alpha = 0.75f;
+  *stop = CBP_STOP_SYNDROME;
+  *soft = nullptr;
+  if (!o) return CBP_OK;
+  if (o->alg < CBP_ALG_CBP_SP || o->alg > CBP_ALG_FBP_SP) return CBP_EINVAL;
+  if (o->stop_mode != CBP_STOP_SYNDROME && o->stop_mode != CBP_STOP_NONE) return CBP_EINVAL;
+  if (!std::isfinite(o->alpha)) return CBP_EINVAL;
+  *alg = o->alg;
+  if (o->alpha > 0.0f) *alpha = o->alpha;
+  *stop = o->stop_mode;
+  *soft = o->soft_out;
+  if (*soft && !aligned(*soft, 4)) return CBP_EINVAL;
+  return CBP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cbp_code_create(const int32_t* base, int mb, int nb, int Z, cbp_code_t** out) {
+  if (!base || !out || mb < 1 || nb < 1 || Z < 1) return CBP_EINVAL;
+  for (long long i = 0; i < 1LL * mb * nb; ++i)
+    if (base[i] < -1 || base[i] >= Z) return CBP_EINVAL;
+  int nnzb = 0, maxdeg = 0;
+  for (int r = 0; r < mb; ++r) {
+    int d = 0;
+    for (int c = 0; c < nb; ++c) d += base[r * nb + c] >= 0;
+    if (d < 2) return CBP_EINVAL;
+    nnzb += d;
+    maxdeg = std::max(maxdeg, d);
+  }
+  for (int c = 0; c < nb; ++c) {
+    int w = 0;
+    for (int r = 0; r < mb; ++r) w += base[r * nb + c] >= 0;
+    if (w < 1) return CBP_EINVAL;
+  }
+  if (Z > 1024 || mb > 4096 || nb > 4096 || nnzb > 65535) return CBP_EUNSUPPORTED;
+  if (1LL * nb * Z > (1LL << 30) / 4) return CBP_EUNSUPPORTED;
+
+  DeviceInfo* di = nullptr;
+  int dev = 0;
+  if (int rc = current_device(&di, &dev)) return rc;
+
+  // row-major entry list with each entry's predecessor in its column
+  std::vector<int> idx(static_cast<size_t>(mb) * nb, -1);
+  std::vector<BaseEdge> edges;
+  std::vector<int> rptr(1, 0);
+  for (int r = 0; r < mb; ++r) {
+    for (int c = 0; c < nb; ++c)
+      if (base[r * nb + c] >= 0) {
+        idx[r * nb + c] = static_cast<int>(edges.size());
+        BaseEdge e{};
+        e.c = static_cast<uint16_t>(c);
+        e.s = static_cast<uint16_t>(base[r * nb + c]);
+        edges.push_back(e);
+      }
+    rptr.push_back(static_cast<int>(edges.size()));
+  }
+  std::vector<ColEntry> cols;
+  std::vector<int> cptr(1, 0);
+  for (int c = 0; c < nb; ++c) {
+    std::vector<int> rows;
+    for (int r = 0; r < mb; ++r)
+      if (base[r * nb + c] >= 0) rows.push_back(r);
+    const int w = static_cast<int>(rows.size());
+    for (int k = 0; k < w; ++k) {
+      const int r = rows[k], pr = rows[(k + w - 1) % w];
+      BaseEdge& e = edges[idx[r * nb + c]];
+      e.pr = static_cast<uint16_t>(pr);
+      e.ps = static_cast<uint16_t>(base[pr * nb + c]);
+      e.pe = static_cast<uint16_t>(idx[pr * nb + c]);
+      e.flags = static_cast<uint16_t>((k == 0 ? kFirst : 0) | (w == 1 ? kSelf : 0));
+      ColEntry ce{};
+      ce.r = static_cast<uint16_t>(r);
+      ce.s = static_cast<uint16_t>(base[r * nb + c]);
+      ce.e = static_cast<uint16_t>(idx[r * nb + c]);
+      cols.push_back(ce);
+    }
+    cptr.push_back(static_cast<int>(cols.size()));
+  }
+
+  cbp_code* c = new (std::nothrow) cbp_code;
+  if (!c) return CBP_ENOMEM;
+  c->dev = dev;
+  c->mb = mb;
+  c->nb = nb;
+  c->Z = Z;
+  c->N = nb * Z;
+  c->M = mb * Z;
+  c->nnzb = nnzb;
+  c->E = nnzb * Z;
+  c->maxdeg = maxdeg;
+  // K = N - rank(H): full rank when the parity part is block lower-triangular with
+  // an identity-shift diagonal in column (nb - mb + r); else eliminate small codes.
+  bool tri = nb > mb;
+  for (int r = 0; r < mb && tri; ++r) {
+    const int p = nb - mb + r;
+    if (base[r * nb + p] < 0) tri = false;
+    for (int cc = p + 1; cc < nb && tri; ++cc)
+      if (base[r * nb + cc] >= 0) tri = false;
+  }
+  if (tri) c->K = c->N - c->M;
+  else if (1LL * c->M * c->N <= (1LL << 24)) c->K = c->N - gf2_rank(base, mb, nb, Z);
+
+  bool ok = cudaMalloc(&c->d.edges, sizeof(BaseEdge) * edges.size()) == cudaSuccess &&
+            cudaMalloc(&c->d.rptr, sizeof(int) * rptr.size()) == cudaSuccess &&
+            cudaMalloc(&c->d.cols, sizeof(ColEntry) * cols.size()) == cudaSuccess &&
+            cudaMalloc(&c->d.cptr, sizeof(int) * cptr.size()) == cudaSuccess;
+  if (!ok) {
+    cbp_code_destroy(c);
+    return CBP_ENOMEM;
+  }
+  ok = cudaMemcpy(c->d.edges, edges.data(), sizeof(BaseEdge) * edges.size(),
+                  cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(c->d.rptr, rptr.data(), sizeof(int) * rptr.size(), cudaMemcpyHostToDevice) ==
+           cudaSuccess &&
+       cudaMemcpy(c->d.cols, cols.data(), sizeof(ColEntry) * cols.size(),
+                  cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(c->d.cptr, cptr.data(), sizeof(int) * cptr.size(), cudaMemcpyHostToDevice) ==
+           cudaSuccess;
+  if (!ok) {
+    cbp_code_destroy(c);
+    return CBP_ECUDA;
+  }
+  *out = c;
+  return CBP_OK;
+}
+
+void cbp_code_destroy(cbp_code_t* c) {
+  if (!c) return;
+  cudaFree(c->d.edges);
+  cudaFree(c->d.rptr);
+  cudaFree(c->d.cols);
+  cudaFree(c->d.cptr);
+  delete c;
+}
+
+int cbp_code_info(const cbp_code_t* c, int* n, int* m, int* k, int* edges) {
+  if (!c) return CBP_EINVAL;
+  if (n) *n = c->N;
+  if (m) *m = c->M;
+  if (k) *k = c->K;
+  if (edges) *edges = c->E;
+  return CBP_OK;
+}
+
+int cbp_workspace_bytes(const cbp_code_t* c, int batch, const cbp_opts_t* opts, size_t* bytes) {
+  if (!c || !bytes || batch < 0) return CBP_EINVAL;
+  int alg, stop;
+  float alpha;
+  float* soft;
+  if (int rc = check_opts(opts, &alg, &alpha, &stop, &soft)) return rc;
+  if (batch == 0) {
+    *bytes = 0;
+    return CBP_OK;
+  }
+  DeviceInfo* di = nullptr;
+  int dev = 0;
+  if (int rc = current_device(&di, &dev)) return rc;
+  if (dev != c->dev) return CBP_EDEVICE;
+  Plan pl;
+  if (int rc = make_plan(c, *di, alg, batch, &pl)) return rc;
+  *bytes = pl.ws_bytes;
+  return CBP_OK;
+}
+
+int cbp_decode_ex(const cbp_code_t* c, const float* llr, uint32_t* hard_out, int32_t* iters_out,
+                  int max_iter, int batch, void* workspace, size_t workspace_bytes,
+                  cbp_stream_t stream, const cbp_opts_t* opts) {
+  if (!c || max_iter < 1 || batch < 0) return CBP_EINVAL;
+  int alg, stop;
+  float alpha;
+  float* soft;
+  if (int rc = check_opts(opts, &alg, &alpha, &stop, &soft)) return rc;
+  if (batch == 0) return CBP_OK;
+  if (!llr || !hard_out || !iters_out || !workspace) return CBP_EINVAL;
+  if (!aligned(llr, 16) || !aligned(hard_out, 4) || !aligned(iters_out, 4) ||
+      !aligned(workspace, 256))
+    return CBP_EINVAL;
+  DeviceInfo* di = nullptr;
+  int dev = 0;
+  if (int rc = current_device(&di, &dev)) return rc;
+  if (dev != c->dev) return CBP_EDEVICE;
+  Plan pl;
+  if (int rc = make_plan(c, *di, alg, batch, &pl)) return rc;
+  if (workspace_bytes < pl.ws_bytes) return CBP_EWORKSPACE;
+
+  KParams p{};
+  p.llr = llr;
+  p.hard = hard_out;
+  p.iters = iters_out;
+  p.soft = soft;
+  p.ws = static_cast<float*>(workspace);
+  p.edges = c->d.edges;
+  p.rptr = c->d.rptr;
+  p.cols = c->d.cols;
+  p.cptr = c->d.cptr;
+  p.phi_tab = di->tab;
+  p.phi_xlo = di->xlo;
+  p.Z = c->Z;
+  p.mb = c->mb;
+  p.nb = c->nb;
+  p.nnzb = c->nnzb;
+  p.N = c->N;
+  p.M = c->M;
+  p.E = c->E;
+  p.words = (c->N + 31) / 32;
+  p.batch = batch;
+  p.max_iter = max_iter;
+  p.stop = stop;
+  p.alpha = alpha;
+  p.F = pl.F;
+  p.slots = pl.grid * pl.F;
+  p.maxdeg = c->maxdeg;
+  p.ws_slot = pl.ws_slot;
+  p.sh_frame = pl.sh_frame;
+  cudaError_t e = launch_decoder(pl.v, p, pl.grid, pl.threads, pl.smem,
+                                 reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? CBP_OK : CBP_ECUDA;
+}
+
+int cbp_decode(const cbp_code_t* c, const float* llr, uint32_t* hard_out, int32_t* iters_out,
+               int max_iter, int batch, void* workspace, size_t workspace_bytes,
+               cbp_stream_t stream) {
+  return cbp_decode_ex(c, llr, hard_out, iters_out, max_iter, batch, workspace,
+                       workspace_bytes, stream, nullptr);
+}
+
+int cbp_phi(const float* x, float* y, int64_t n, cbp_stream_t stream) {
+  if (n < 0) return CBP_EINVAL;
+  if (n == 0) return CBP_OK;
+  if (!x || !y || !aligned(x, 4) || !aligned(y, 4)) return CBP_EINVAL;
+  DeviceInfo* di = nullptr;
+  if (int rc = current_device(&di, nullptr)) return rc;
+  return launch_phi(x, y, n, di->tab, di->xlo, reinterpret_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? CBP_OK
+             : CBP_ECUDA;
+}
+
+const char* cbp_strerror(int s) {
+  switch (s) {
+    case CBP_OK: return "success";
+    case CBP_EINVAL: return "invalid argument";
+    case CBP_ENOMEM: return "device allocation failed";
+    case CBP_ECUDA: return "CUDA runtime or launch error";
+    case CBP_EUNSUPPORTED: return "unsupported code size or option";
+    case CBP_EWORKSPACE: return "workspace too small";
+    case CBP_EDEVICE: return "code handle belongs to another device";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

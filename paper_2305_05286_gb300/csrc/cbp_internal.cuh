@@ -1,0 +1,118 @@
+// Internal declarations shared by the libcbp translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "cbp.h"
+
+namespace cbp {
+
+// ----------------------------------------------------------------------------
+// phi(x) = -log tanh(x/2), Eq. (s2e5), in FP32.
+// phi(clamp(x, X_LO, 30)) with X_LO = fl32(phi(30)); cubic Taylor polynomial around
+// the nearest grid centre: below 2 the FP32 values whose low 18 mantissa bits are
+// zero (bit patterns (2688 + i) << 18, i = 0..1408, i.e. 2^-43 .. 2.0), local variable
+// t = (x - centre) / 2^e(centre); from 2 to 30 the centres k/16, t = 16x - k.
+// ----------------------------------------------------------------------------
+constexpr int kPhiLogBase = 2688;
+constexpr int kPhiLogCount = 1409;
+constexpr int kPhiSegments = kPhiLogCount + 449;
+
+// Host: fill the coefficient table (4 floats per centre) and the lower clamp.
+void phi_table_host(float* coef, float* xlo);
+
+__device__ __forceinline__ float phi_eval(float x, float xlo, const float4* __restrict__ tab) {
+  x = fminf(fmaxf(x, xlo), 30.0f);
+  const uint32_t cb = (__float_as_uint(x) + 0x20000u) & 0xFFFC0000u;
+  const float u = __fmul_rn(x, 16.0f);
+  const float k = rintf(u);
+  const bool lo = x < 2.0f;
+  const float tl = __fmul_rn(__fsub_rn(x, __uint_as_float(cb)),
+                             __uint_as_float((254u - (cb >> 23)) << 23));
+  const float t = lo ? tl : __fsub_rn(u, k);
+  const int i = lo ? static_cast<int>(cb >> 18) - kPhiLogBase
+                   : static_cast<int>(k) + (kPhiLogCount - 32);
+  const float4 c = tab[i];
+  float p = __fmaf_rn(c.w, t, c.z);
+  p = __fmaf_rn(p, t, c.y);
+  return __fmaf_rn(p, t, c.x);
+}
+
+// ----------------------------------------------------------------------------
+// Code tables (built on the host by cbp_code_create).
+// ----------------------------------------------------------------------------
+// One entry per non-zero base entry, row-major, ascending column inside a row.
+struct BaseEdge {
+  uint16_t c;      // base column
+  uint16_t s;      // shift
+  uint16_t pr;     // predecessor row: the previous row (cyclically) holding column c
+  uint16_t ps;     // shift of the predecessor entry
+  uint16_t pe;     // index of the predecessor entry in this list
+  uint16_t flags;  // kFirst: r is the first row of column c; kSelf: c has weight 1
+  uint32_t pad;
+};
+constexpr uint16_t kFirst = 1, kSelf = 2;
+
+// Column-major view: the rows of column c in ascending order (flooding posterior).
+struct ColEntry {
+  uint16_t r, s, e, pad;
+};
+
+struct CodeDev {
+  BaseEdge* edges = nullptr;  // [nnzb]
+  int* rptr = nullptr;        // [mb + 1]
+  ColEntry* cols = nullptr;   // [nnzb], column-major
+  int* cptr = nullptr;        // [nb + 1]
+};
+
+// Kernel parameters (passed by value).
+struct KParams {
+  const float* llr;
+  uint32_t* hard;
+  int32_t* iters;
+  float* soft;
+  float* ws;
+  const BaseEdge* edges;
+  const int* rptr;
+  const ColEntry* cols;
+  const int* cptr;
+  const float4* phi_tab;
+  float phi_xlo;
+  int Z, mb, nb, nnzb, N, M, E, words;
+  int batch, max_iter, stop;
+  float alpha;
+  int F;                 // frames per CTA
+  int slots;             // gridDim.x * F
+  int maxdeg;
+  long long ws_slot;     // floats of workspace per frame slot
+  int sh_frame;          // floats of shared memory per frame
+};
+
+enum Alg { ALG_CBP_SP = 0, ALG_CBP_NMS = 1, ALG_LBP_NMS = 2, ALG_FBP_SP = 3 };
+
+struct Variant {
+  int alg;
+  bool phi_cache;   // keep phi(|Q*|) per variable in shared memory (CBP-SP)
+  bool chk_shared;  // check state in shared memory (else in the workspace)
+};
+
+// Shared-memory and workspace layout of one launch.
+size_t shared_fixed_bytes(const Variant& v, int nnzb, int mb, int nb, int F);
+size_t shared_frame_floats(const Variant& v, int N, int M, int words);
+size_t ws_slot_floats(const Variant& v, int N, int M, int E);
+
+// Launchers (cbp_layered.cu / cbp_flood.cu).
+cudaError_t launch_decoder(const Variant& v, const KParams& p, int grid, int threads,
+                           size_t smem, cudaStream_t st);
+cudaError_t decoder_func_attrs(const Variant& v, cudaFuncAttributes* a);
+cudaError_t decoder_set_smem(const Variant& v, int bytes);
+cudaError_t decoder_occupancy(const Variant& v, int threads, size_t smem, int* ctas);
+cudaError_t launch_phi(const float* x, float* y, long long n, const float4* tab, float xlo,
+                       cudaStream_t st);
+
+constexpr int kMaxDeg = 32;  // row-degree limit of the two-pass (pooled) comparators
+
+}  // namespace cbp

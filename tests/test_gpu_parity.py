@@ -1,0 +1,213 @@
+"""GPU decoders (through the C ABI) against the CPU oracle, element by element.
+
+The oracle (FP32) and libcbp implement the same operation order and the same phi,
+so hard decisions, iteration counts and soft outputs must agree bit for bit; that
+is stricter than identical decisions/iterations plus soft outputs within 1e-5.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2305_05286_gb300 import cbp
+from paper_2305_05286_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 1
+ALGS = ["cbp_sp", "cbp_nms", "lbp_nms", "fbp_sp"]
+
+
+def run_gpu(code, llr, alg, max_iter=30, stop="syndrome", alpha=0.75):
+    x = torch.from_numpy(np.ascontiguousarray(llr)).cuda()
+    hard, iters, soft = code.decode(x, max_iter=max_iter, alg=alg, alpha=alpha, stop=stop, soft=True)
+    torch.cuda.synchronize()
+    return (cbp.unpack_bits(hard, code.N).cpu().numpy(), iters.cpu().numpy(), soft.cpu().numpy())
+
+
+def assert_parity(got, ref, what=""):
+    hard, iters, soft = got
+    assert np.array_equal(iters, ref["iters"]), f"{what}: iteration counts differ"
+    assert np.array_equal(hard, ref["hard"]), f"{what}: hard decisions differ"
+    diff = np.abs(soft.astype(np.float64) - ref["soft"].astype(np.float64))
+    assert diff.max() <= 1e-5, f"{what}: soft outputs differ by {diff.max()}"
+    assert np.array_equal(soft, ref["soft"]), f"{what}: soft outputs not bitwise equal"
+
+
+@pytest.fixture(scope="module")
+def code576():
+    qc = I.code_576()
+    return qc, cbp.Code.from_qc(qc), O.OracleCode(qc.base, qc.Z)
+
+
+def test_phi_bitwise_equal_to_oracle():
+    lo = np.float32(O.xlo32()).view(np.uint32)
+    hi = np.float32(30.0).view(np.uint32)
+    bits = np.arange(lo - 4096, hi + 4096, 61, dtype=np.uint32)
+    x = np.concatenate([bits.view(np.float32),
+                        np.array([0.0, 1e-30, 2.0, 30.0, 1e4, np.inf, np.nan], np.float32)])
+    y = cbp.phi(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = O.phi32(x)
+    assert np.array_equal(y.view(np.uint32), ref.view(np.uint32))
+
+
+@pytest.mark.parametrize("ebn0", [1.5, 2.0, 2.5])
+@pytest.mark.parametrize("alg", ALGS)
+def test_parity_576_2000_frames(code576, alg, ebn0):
+    qc, code, oc = code576
+    fr = I.make_frames(qc, 2000, ebn0, seed=1000 + int(round(ebn0 * 10)))
+    ref = oc.decode(fr.llr, alg=alg, max_iter=30, threads=THREADS)
+    assert_parity(run_gpu(code, fr.llr, alg), ref, f"{alg} @ {ebn0} dB")
+    if alg == "cbp_sp":
+        assert (ref["iters"] > 0).mean() > 0.5
+
+
+@pytest.mark.parametrize("batch", [1, 3, 25, 151, 152, 153, 1000])
+def test_ragged_batches_576(code576, batch):
+    qc, code, oc = code576
+    fr = I.make_frames(qc, batch, 1.75, seed=77 + batch)
+    for alg in ALGS:
+        ref = oc.decode(fr.llr, alg=alg, max_iter=20, threads=THREADS)
+        assert_parity(run_gpu(code, fr.llr, alg, max_iter=20), ref, f"{alg} batch {batch}")
+
+
+@pytest.mark.parametrize("max_iter,stop", [(1, "syndrome"), (2, "none"), (7, "none")])
+def test_sweep_limits_and_fixed_sweeps(code576, max_iter, stop):
+    qc, code, oc = code576
+    fr = I.make_frames(qc, 300, 2.0, seed=500 + max_iter)
+    for alg in ALGS:
+        ref = oc.decode(fr.llr, alg=alg, max_iter=max_iter, stop=stop, threads=THREADS)
+        assert_parity(run_gpu(code, fr.llr, alg, max_iter=max_iter, stop=stop), ref, alg)
+
+
+@pytest.mark.parametrize("Z", [1, 4, 7, 32, 33])
+def test_other_liftings(code576, Z):
+    """Same base graph lifted by other Z (several frames per warp, Z > 32, Z = 1)."""
+    qc = I.relift(code576[0], Z)
+    code = cbp.Code.from_qc(qc)
+    oc = O.OracleCode(qc.base, qc.Z)
+    fr = I.make_frames(qc, 257, 2.5, seed=900 + Z, encoder="zero")
+    for alg in ALGS:
+        ref = oc.decode(fr.llr, alg=alg, max_iter=15, threads=THREADS)
+        assert_parity(run_gpu(code, fr.llr, alg, max_iter=15), ref, f"{alg} Z={Z}")
+
+
+def test_parity_2304():
+    qc = I.code_2304()
+    code = cbp.Code.from_qc(qc)
+    oc = O.OracleCode(qc.base, qc.Z)
+    fr = I.make_frames(qc, 400, 1.75, seed=6017)
+    for alg in ALGS:
+        ref = oc.decode(fr.llr, alg=alg, max_iter=10, threads=THREADS)
+        assert_parity(run_gpu(code, fr.llr, alg, max_iter=10), ref, alg)
+
+
+@pytest.fixture(scope="module")
+def large():
+    qc = I.code_26112()
+    return qc, cbp.Code.from_qc(qc), O.OracleCode(qc.base, qc.Z)
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_parity_26112_small_batch(large, alg):
+    qc, code, oc = large
+    llr, cw = I.make_frames_torch(qc, 96, 0.75, seed=2075)
+    ref = oc.decode(llr.cpu().numpy(), alg=alg, max_iter=20, threads=THREADS)
+    assert_parity(run_gpu(code, llr.cpu().numpy(), alg, max_iter=20), ref, alg)
+
+
+def gpu_syndrome(qc, hard_bits):
+    """H x^T on the GPU with torch gathers (independent of libcbp)."""
+    rows = torch.from_numpy(np.stack([np.pad(r, (0, 32 - len(r)), constant_values=-1)
+                                      for r in qc.check_rows()])).cuda()
+    valid = rows >= 0
+    g = hard_bits[:, rows.clamp(min=0)] * valid
+    return g.sum(dim=2) & 1
+
+
+def test_full_size_26112_sampled(large):
+    """65536 frames in the benchmark's launch configuration; 12 frames re-decoded by the oracle."""
+    qc, code, oc = large
+    B = 65536
+    llr, cw = I.make_frames_torch(qc, B, 1.0, seed=2100)
+    hard, iters, soft = code.decode(llr, max_iter=20, alg="cbp_sp", soft=True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    pick = np.concatenate([[0, 1, B // 2, B - 2, B - 1], rng.choice(B, 7, replace=False)])
+    sub = llr[torch.from_numpy(pick).cuda()].cpu().numpy()
+    ref = oc.decode(sub, alg="cbp_sp", max_iter=20, threads=THREADS)
+    got = (cbp.unpack_bits(hard[pick], qc.N).cpu().numpy(), iters[pick].cpu().numpy(),
+           soft[pick].cpu().numpy())
+    assert_parity(got, ref, "26112 sampled")
+    # properties at full size: converged frames satisfy every check, others do not
+    bitsu = cbp.unpack_bits(hard[:2048], qc.N).to(torch.int32)
+    syn = gpu_syndrome(qc, bitsu).any(dim=1).cpu().numpy()
+    it = iters[:2048].cpu().numpy()
+    assert not syn[it > 0].any() and syn[it < 0].all()
+    assert ((np.abs(iters.cpu().numpy()) >= 1) & (np.abs(iters.cpu().numpy()) <= 20)).all()
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_sign_symmetry_on_gpu(code576, alg):
+    qc, code, oc = code576
+    fr = I.make_frames(qc, 200, 2.0, seed=31, encoder="zero")
+    enc = I.GF2Encoder(qc)
+    cw = enc.encode(np.random.default_rng(8).integers(0, 2, size=(200, enc.K), dtype=np.uint8))
+    flip = (1.0 - 2.0 * cw).astype(np.float32)
+    a = run_gpu(code, fr.llr, alg)
+    b = run_gpu(code, fr.llr * flip, alg)
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[0] ^ cw, b[0])
+    assert np.array_equal(a[2] * flip, b[2])
+
+
+def test_tree_code_on_gpu():
+    base = -np.ones((5, 10), np.int32)
+    for r, vs in enumerate([(0, 1, 2), (2, 3, 4), (4, 5, 6), (1, 7), (6, 8, 9)]):
+        base[r, list(vs)] = 0
+    code = cbp.Code(base, 1)
+    oc = O.OracleCode(base, 1)
+    llr = np.random.default_rng(2).normal(1.0, 1.5, size=(64, 10)).astype(np.float32)
+    for alg in ALGS:
+        assert_parity(run_gpu(code, llr, alg, max_iter=12, stop="none"),
+                      oc.decode(llr, alg=alg, max_iter=12, stop="none"), alg)
+
+
+def test_error_paths(code576):
+    qc, code, oc = code576
+    x = torch.zeros((8, qc.N), dtype=torch.float32, device="cuda")
+    hard = torch.full((8, code.words), 7, dtype=torch.int32, device="cuda")
+    iters = torch.full((8,), 7, dtype=torch.int32, device="cuda")
+    need = code.workspace_bytes(8)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    L = cbp.lib()
+    s = torch.cuda.current_stream().cuda_stream
+    assert L.cbp_decode(code._h, x.data_ptr(), hard.data_ptr(), iters.data_ptr(), 30, 8,
+                        ws.data_ptr(), need - 1, s) == -5
+    assert L.cbp_decode(code._h, x.data_ptr() + 4, hard.data_ptr(), iters.data_ptr(), 30, 8,
+                        ws.data_ptr(), need, s) == -1
+    assert L.cbp_decode(code._h, x.data_ptr(), hard.data_ptr(), iters.data_ptr(), 0, 8,
+                        ws.data_ptr(), need, s) == -1
+    assert L.cbp_decode(code._h, x.data_ptr(), hard.data_ptr(), iters.data_ptr(), 30, 0,
+                        ws.data_ptr(), need, s) == 0
+    torch.cuda.synchronize()
+    assert (hard == 7).all() and (iters == 7).all()     # nothing launched
+    big = np.zeros((1, 40), np.int32)                    # row degree 40 > 32
+    bigc = cbp.Code(np.vstack([big, big]), 3)
+    with pytest.raises(cbp.CbpError):
+        bigc.workspace_bytes(4, alg="lbp_nms")
+    assert bigc.workspace_bytes(4, alg="cbp_sp") > 0     # CBP has no per-row pool limit
+
+
+def test_wide_rows_cbp_only():
+    """Row degree 40: CBP has no per-row register pool, so it decodes; the oracle agrees."""
+    rng = np.random.default_rng(12)
+    base = np.where(rng.random((4, 48)) < 0.85, rng.integers(0, 8, (4, 48)), -1).astype(np.int32)
+    base[:, :2] = 0
+    base[0, 2:] = np.where(base[0, 2:] < 0, 3, base[0, 2:])
+    qc = I.QCCode(base, 8)
+    code = cbp.Code.from_qc(qc)
+    oc = O.OracleCode(base, 8)
+    llr = (3.0 + 2.0 * rng.standard_normal((40, qc.N))).astype(np.float32)
+    for alg in ("cbp_sp", "cbp_nms"):
+        assert_parity(run_gpu(code, llr, alg, max_iter=8), oc.decode(llr, alg=alg, max_iter=8), alg)
