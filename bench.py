@@ -1,0 +1,406 @@
+"""Throughput benchmark of CBP decoding on one GB300 (or N replicas under torchrun).
+
+Workload: the 46x68 base graph lifted by Z=384 (N=26112, K=8448, rate 22/68),
+65536 BPSK/AWGN frames per launch, at most 20 sweeps, syndrome stop.  One step is
+one cbp_decode_ex launch over the whole batch with the LLRs resident in HBM
+(6.85 GB per launch, far larger than L2).  Reported: decoded (information) Gbit/s,
+FER/BER/iterations, the same-GPU comparators, an end-to-end number through host
+buffers, an ALU roofline fraction, and the CPU oracle timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --sweep            # FER/BER/iterations/Gbit/s per Eb/N0 point
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CBP decoded Gbit/s at fixed FER vs same-GPU layered min-sum; % of roofline"
+# Operating point: the Eb/N0 grid point (0.25 dB grid) at which layered normalized
+# min-sum (alpha = 0.75) first reaches FER <= 1e-2 on this code.
+EBN0_OPERATING = 2.5
+FRAMES = 65536
+MAX_ITER = 20
+
+# Algorithmic lane operations per unit (derived in the design doc):
+#   phi evaluation 14; CBP-SP edge update 40 (B2V 16, V2C 2, C2B 16, indexing 6);
+#   flush per variable 18; syndrome per edge 3.
+OPS_PHI = 14
+OPS_EDGE = {"cbp_sp": 40, "cbp_nms": 16, "lbp_nms": 14, "fbp_sp": 44}
+OPS_VAR = {"cbp_sp": 18, "cbp_nms": 8, "lbp_nms": 2, "fbp_sp": 3}
+OPS_SYN = 3
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in getattr(self, "lines", []):
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_identity(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev)
+
+
+def timed_steps(torch, fn, steps, stream):
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        fn()
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end) / steps  # ms per step
+
+
+def frame_stats(torch, cbp, qc, hard, iters, cw):
+    bits = cbp.unpack_bits(hard, qc.N)
+    err = bits != cw
+    fer = err.any(dim=1).float().mean().item()
+    ber = err.float().mean().item()
+    it = iters.abs().to(torch.float64)
+    return {"fer": fer, "ber": ber, "mean_iters": it.mean().item(),
+            "sweeps_total": int(it.sum().item()),
+            "unconverged": int((iters < 0).sum().item())}
+
+
+def alu_ops(alg, qc, sweeps_total):
+    per_sweep = qc.E * (OPS_EDGE[alg] + OPS_SYN) + qc.N * OPS_VAR[alg]
+    return per_sweep * sweeps_total
+
+
+def cpu_oracle_rate(qc, llr_host, seconds=12.0, chunk=64):
+    """Time the CPU oracle (all host cores) on consecutive frames until `seconds` pass."""
+    from oracle import oracle as orc
+
+    oc = orc.OracleCode(qc.base, qc.Z)
+    cores = os.cpu_count() or 1
+    done, t0 = 0, time.perf_counter()
+    while True:
+        sub = llr_host[done:done + chunk]
+        if sub.shape[0] == 0:
+            break
+        oc.decode(sub, alg="cbp_sp", max_iter=MAX_ITER, soft=False, threads=cores)
+        done += sub.shape[0]
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    K = (qc.nb - qc.mb) * qc.Z
+    return {"value": K * done / dt / 1e9, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {done} frames of the same batch, FP32 oracle, CBP-SP, "
+                      f"{cores} threads, {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------------------
+def run_reference(args, rank):
+    """The CPU oracle as it stands, on the host cores, same config and metric."""
+    if rank != 0:
+        return
+    from paper_2305_05286_gb300 import inputs as I
+    from oracle import oracle as orc
+
+    qc = I.code_26112()
+    K = (qc.nb - qc.mb) * qc.Z
+    per_step = args.ref_frames
+    fr = I.make_frames(qc, per_step * (args.steps + args.warmup), args.ebn0, seed=9000,
+                       encoder="tri")
+    oc = orc.OracleCode(qc.base, qc.Z)
+    cores = os.cpu_count() or 1
+    times = []
+    for s in range(args.warmup + args.steps):
+        sub = fr.llr[s * per_step:(s + 1) * per_step]
+        t0 = time.perf_counter()
+        oc.decode(sub, alg="cbp_sp", max_iter=MAX_ITER, soft=False, threads=cores)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = K * per_step / (ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "impl": "reference",
+        "config": workload_config(args, qc, note=f"{per_step} frames per step on the host cores"),
+        "cpu_baseline": {"value": value, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} frames per step, FP32 oracle CBP-SP, {cores} threads"},
+        "e2e": {"value": value, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, qc, note=None):
+    c = {"workload": f"QC-LDPC 46x68 base, Z=384 (N={qc.N}, K={(qc.nb - qc.mb) * qc.Z}), "
+                     f"{args.frames} BPSK/AWGN frames per launch at Eb/N0 {args.ebn0} dB, "
+                     f"max {MAX_ITER} sweeps, syndrome stop",
+         "alg": args.alg, "frames_per_launch": args.frames, "ebn0_db": args.ebn0,
+         "max_iter": MAX_ITER, "parallelism": "replicas" if args.gpus > 1 else "single",
+         "l2": "inputs larger than L2 (LLRs 4*N bytes per frame, 6.85 GB per launch)"}
+    if note:
+        c["note"] = note
+    return c
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_2305_05286_gb300 import cbp
+    from paper_2305_05286_gb300 import inputs as I
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    stream = torch.cuda.current_stream(dev)
+    qc = I.code_26112()
+    K = (qc.nb - qc.mb) * qc.Z
+    code = cbp.Code.from_qc(qc)
+    B = args.frames
+    llr, cw = I.make_frames_torch(qc, B, args.ebn0, seed=2000 + 97 * rank, device=dev)
+    hard = torch.empty((B, code.words), dtype=torch.int32, device=dev)
+    iters = torch.empty((B,), dtype=torch.int32, device=dev)
+    ws = code.workspace(B, args.alg)
+
+    def step(alg=args.alg):
+        code.decode_into(llr, hard, iters, max_iter=MAX_ITER, alg=alg, workspace=ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    with ClockSampler(gpu_identity(torch, local)) as clk:
+        torch.cuda.synchronize()
+        ms = timed_steps(torch, step, args.steps, stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st = frame_stats(torch, cbp, qc, hard, iters, cw)
+    value = world * K * B / (ms / 1e3) / 1e9
+
+    peaks = load_peaks()
+    clocks = clk.summary()
+    sm_mhz = clocks["sm_mhz"] or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1455.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_ops = sms * 128 * sm_mhz * 1e6 / 1e12  # T lane-ops/s at the sampled SM clock
+    ops = alu_ops(args.alg, qc, st["sweeps_total"])
+    achieved = ops / (ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
+                "frac": achieved / peak_ops, "traffic": args.traffic,
+                "peak_source": f"{sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (sampled SM clock)",
+                "units": {"edge_sweeps": qc.E * st["sweeps_total"],
+                          "ops_per_edge": OPS_EDGE[args.alg] + OPS_SYN,
+                          "ops_per_var": OPS_VAR[args.alg]}}
+    hbm_bytes = B * (4 * qc.N + 4 * code.words + 4)
+    roofline["hbm_algorithmic_GBs"] = hbm_bytes / (ms / 1e3) / 1e9
+    roofline["hbm_peak_GBs"] = peaks.get("hbm_gbs")
+
+    comparators = {}
+    if not args.no_comparators:
+        for alg in ("cbp_nms", "lbp_nms", "fbp_sp"):
+            if alg == args.alg:
+                continue
+            wsa = code.workspace(B, alg)
+            f = lambda a=alg, w=wsa: code.decode_into(llr, hard, iters, max_iter=MAX_ITER,
+                                                      alg=a, workspace=w)
+            f()
+            torch.cuda.synchronize()
+            cms = timed_steps(torch, f, 2, stream)
+            cs = frame_stats(torch, cbp, qc, hard, iters, cw)
+            comparators[alg] = {"gbps": K * B / (cms / 1e3) / 1e9, "ms_per_step": cms,
+                                "fer": cs["fer"], "ber": cs["ber"], "mean_iters": cs["mean_iters"]}
+        ws = code.workspace(B, args.alg)
+
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty((B, qc.N), dtype=torch.float32, pin_memory=True)
+        host.copy_(llr)
+        x = torch.empty_like(llr)
+        hard_h = torch.empty((B, code.words), dtype=torch.int32, pin_memory=True)
+        iters_h = torch.empty((B,), dtype=torch.int32, pin_memory=True)
+
+        def e2e_step():
+            x.copy_(host, non_blocking=True)
+            code.decode_into(x, hard, iters, max_iter=MAX_ITER, alg=args.alg, workspace=ws)
+            hard_h.copy_(hard, non_blocking=True)
+            iters_h.copy_(iters, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ems = timed_steps(torch, e2e_step, args.steps, stream)
+        if dist:
+            t = torch.tensor([ems], dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * K * B / (ems / 1e3) / 1e9, "unit": "Gbit/s",
+               "h2d_bytes_per_step": B * qc.N * 4,
+               "d2h_bytes_per_step": B * code.words * 4 + B * 4, "ms_per_step": ems}
+        del host, hard_h, iters_h, x
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = llr[: args.cpu_frames].cpu().numpy()
+        cpu = cpu_oracle_rate(qc, sample, seconds=args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(args, qc),
+            "fer": st["fer"], "ber": st["ber"], "mean_iters": st["mean_iters"],
+            "unconverged_frames": st["unconverged"],
+            "coded_gbps": world * qc.N * B / (ms / 1e3) / 1e9,
+            "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps,
+            "roofline": roofline, "cpu_baseline": cpu, "comparators": comparators,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def run_sweep(args):
+    import torch
+
+    from paper_2305_05286_gb300 import cbp
+    from paper_2305_05286_gb300 import inputs as I
+
+    qc = I.code_26112()
+    K = (qc.nb - qc.mb) * qc.Z
+    code = cbp.Code.from_qc(qc)
+    B = args.sweep_frames
+    stream = torch.cuda.current_stream()
+    rows = []
+    for i, e in enumerate(np.arange(args.sweep_lo, args.sweep_hi + 1e-9, 0.25)):
+        llr, cw = I.make_frames_torch(qc, B, float(e), seed=2000 + i)
+        hard = torch.empty((B, code.words), dtype=torch.int32, device="cuda")
+        iters = torch.empty((B,), dtype=torch.int32, device="cuda")
+        for alg in ("cbp_sp", "cbp_nms", "lbp_nms", "fbp_sp"):
+            ws = code.workspace(B, alg)
+            f = lambda: code.decode_into(llr, hard, iters, max_iter=MAX_ITER, alg=alg, workspace=ws)
+            f()
+            torch.cuda.synchronize()
+            ms = timed_steps(torch, f, 1, stream)
+            s = frame_stats(torch, cbp, qc, hard, iters, cw)
+            row = {"ebn0_db": float(e), "alg": alg, "frames": B, "fer": s["fer"], "ber": s["ber"],
+                   "mean_iters": s["mean_iters"], "gbps": K * B / (ms / 1e3) / 1e9, "ms": ms}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+        del llr, cw
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--alg", default="cbp_sp", choices=["cbp_sp", "cbp_nms", "lbp_nms", "fbp_sp"])
+    ap.add_argument("--ebn0", type=float, default=EBN0_OPERATING)
+    ap.add_argument("--frames", type=int, default=FRAMES)
+    ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--sweep-frames", type=int, default=16384)
+    ap.add_argument("--sweep-lo", type=float, default=0.0)
+    ap.add_argument("--sweep-hi", type=float, default=2.0)
+    ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-frames", type=int, default=4096)
+    ap.add_argument("--ref-frames", type=int, default=64)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch from an ncu capture of the current kernel")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+
+        td.init_process_group("gloo")
+        dist = td
+    args.gpus = world if world > 1 else args.gpus
+    if args.impl == "reference":
+        run_reference(args, rank)
+    elif args.sweep:
+        run_sweep(args)
+    else:
+        run_ours(args, rank, world, dist)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

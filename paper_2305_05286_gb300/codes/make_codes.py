@@ -25,7 +25,8 @@ def main():
                      "Rows 0-3 x columns 22-25: dual-diagonal (lower bidiagonal) core, shift 0.\n"
                      "Rows 4-45: weight-1 extension column 22+r, shift 0.\n"
                      "Info columns (all rows) and core parity columns (extension rows): density 0.25,\n"
-                     "shifts uniform in [0,Z), 4-cycles rejected.")
+                     "shifts uniform in [0,Z), 4-cycles rejected; then every info column is topped up\n"
+                     "to two entries in the core rows 0-3.")
 
 
 if __name__ == "__main__":

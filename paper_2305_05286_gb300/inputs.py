@@ -169,7 +169,7 @@ def make_dual_diagonal_code(mb: int, nb: int, Z: int, col_weight: int, seed: int
 
 
 def make_extension_code(mb: int, nb: int, kb: int, core: int, Z: int, density: float,
-                        seed: int) -> np.ndarray:
+                        seed: int, min_core: int = 2) -> np.ndarray:
     """Base graph with a dual-diagonal core and weight-1 extension columns.
 
     Rows 0..core-1 x columns kb..kb+core-1: lower bidiagonal (shift 0).
@@ -177,7 +177,10 @@ def make_extension_code(mb: int, nb: int, kb: int, core: int, Z: int, density: f
     Every other entry of the info columns 0..kb-1 (all rows) and of the core
     parity columns (extension rows) is present with probability ``density``,
     with a shift uniform in [0, Z) resampled while it closes a 4-cycle.
-    Draw order: rows ascending, columns ascending.
+    Draw order: rows ascending, columns ascending.  Then every info column is
+    topped up to ``min_core`` entries in the core rows (random core rows, same
+    generator): an info column absent from the core would form, with its
+    weight-1 extension parities, codewords of weight 1 + (column weight).
     """
     if nb != kb + mb:
         raise ValueError("nb must equal kb + mb")
@@ -206,6 +209,11 @@ def make_extension_code(mb: int, nb: int, kb: int, core: int, Z: int, density: f
         while (base[:, c] >= 0).sum() < 1:
             r = int(rng.integers(mb))
             _place(base, Z, r, c, rng)
+    for c in range(kb):
+        while (base[:core, c] >= 0).sum() < min(min_core, core):
+            r = int(rng.integers(core))
+            if base[r, c] < 0:
+                _place(base, Z, r, c, rng)
     return base
 
 
@@ -267,10 +275,6 @@ def relift(code: QCCode, Z: int) -> QCCode:
 # ----------------------------------------------------------------------------
 # encoders
 # ----------------------------------------------------------------------------
-def info_length(code: QCCode) -> int:
-    return code.N - gf2_rank_dense(code.dense_H()) if code.N <= 8192 else (code.nb - code.mb) * code.Z
-
-
 def is_lower_triangular(code: QCCode) -> bool:
     """Row r's parity block is column kb + r and every other entry lies left of it."""
     kb = code.nb - code.mb

@@ -7,7 +7,7 @@ from paper_2305_05286_gb300 import inputs as I
 
 @pytest.mark.parametrize("fn,N,M,E,Z", [(I.code_576, 576, 288, 1416, 24),
                                          (I.code_2304, 2304, 1152, 5664, 96),
-                                         (I.code_26112, 26112, 17664, 132480, 384)])
+                                         (I.code_26112, 26112, 17664, 141312, 384)])
 def test_committed_codes(fn, N, M, E, Z):
     c = fn()
     assert (c.N, c.M, c.E, c.Z) == (N, M, E, Z)
