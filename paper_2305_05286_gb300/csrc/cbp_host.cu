@@ -1,6 +1,7 @@
 // libcbp host side: the C ABI of include/cbp.h, code tables, phi table, launch planning.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -78,10 +79,8 @@ int device_init(int dev, DeviceInfo** out) {
         cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
             cudaSuccess)
       return CBP_ECUDA;
-    const Variant all[] = {{ALG_CBP_SP, true, true},  {ALG_CBP_SP, true, false},
-                           {ALG_CBP_SP, false, true}, {ALG_CBP_SP, false, false},
-                           {ALG_CBP_NMS, false, true}, {ALG_CBP_NMS, false, false},
-                           {ALG_LBP_NMS, false, true}, {ALG_FBP_SP, false, false}};
+    const Variant all[] = {{ALG_CBP_SP, true},   {ALG_CBP_SP, false}, {ALG_CBP_NMS, true},
+                           {ALG_CBP_NMS, false}, {ALG_LBP_NMS, true}, {ALG_FBP_SP, false}};
     for (const Variant& v : all)
       if (decoder_set_smem(v, d.smem_optin) != cudaSuccess) return CBP_ECUDA;
     d.tab = static_cast<float4*>(addr);
@@ -101,40 +100,53 @@ int current_device(DeviceInfo** out, int* dev_out) {
 
 }  // namespace
 
-size_t shared_fixed_bytes(const Variant& v, int nnzb, int mb, int nb, int F) {
-  size_t b = 0;
-  if (v.alg == ALG_CBP_SP || v.alg == ALG_FBP_SP) b += sizeof(float4) * kPhiSegments;
-  b += sizeof(BaseEdge) * nnzb;
-  b += sizeof(int) * ((mb + 1 + 3) & ~3);
-  if (v.alg == ALG_FBP_SP) {
-    b += sizeof(ColEntry) * ((nnzb + 1) & ~1);
-    b += sizeof(int) * ((nb + 1 + 3) & ~3);
-  } else {
-    b += sizeof(uint32_t) * ((nb + 3) & ~3);
+namespace {
+size_t align4(size_t n) { return (n + 3) & ~static_cast<size_t>(3); }
+size_t align64(size_t n) { return (n + 63) & ~static_cast<size_t>(63); }
+}  // namespace
+
+size_t shared_fixed_bytes(const Variant& v, const Shape& s, int F) {
+  size_t b = sizeof(BaseEdge) * s.nnzb + sizeof(int) * align4(s.mb + 1) + 12 * align4(F);
+  switch (v.alg) {
+    case ALG_CBP_SP:
+      b += sizeof(float4) * kPhiSegments + sizeof(uint2) * ((s.nb + 1) & ~1);
+      break;
+    case ALG_FBP_SP:
+      b += sizeof(float4) * kPhiSegments + sizeof(ColEntry) * ((s.nnzb + 1) & ~1) +
+           sizeof(int) * align4(s.nb + 1);
+      break;
+    default:
+      b += sizeof(uint32_t) * align4(s.nb);
   }
-  b += 12 * ((F + 3) & ~3);
   return b;
 }
 
-size_t shared_frame_floats(const Variant& v, int N, int M, int words) {
-  const size_t Np = (N + 3) & ~3, Mp = (M + 3) & ~3, Wp = (words + 3) & ~3;
-  size_t f = Np + Wp;
-  if (v.alg == ALG_CBP_SP && v.phi_cache) f += Np;
-  if (v.chk_shared) {
-    if (v.alg == ALG_CBP_SP) f += Mp;
-    if (v.alg == ALG_CBP_NMS) f += 2 * Mp;
+size_t shared_frame_floats(const Variant& v, const Shape& s) {
+  const size_t W = align4(s.words);
+  switch (v.alg) {
+    case ALG_CBP_SP:
+      return 2 * static_cast<size_t>(s.ncomp) * s.Z + (v.chk_shared ? align4(s.M) : 0) + W;
+    case ALG_CBP_NMS:
+      return align4(s.N) + (v.chk_shared ? 2 * align4(s.M) : 0) + W;
+    default:
+      return align4(s.N) + W;
   }
-  return f;
 }
 
-size_t ws_slot_floats(const Variant& v, int N, int M, int E) {
-  (void)N;
-  size_t f = E;
-  if (!v.chk_shared) {
-    if (v.alg == ALG_CBP_SP) f += M;
-    if (v.alg == ALG_CBP_NMS) f += 2 * static_cast<size_t>(M);
+size_t ws_slot_floats(const Variant& v, const Shape& s, long long* off_sv, long long* off_s) {
+  size_t f = align64(s.E);
+  *off_sv = *off_s = 0;
+  if (v.alg == ALG_CBP_SP) {
+    *off_sv = static_cast<long long>(f);
+    f += align64(2 * static_cast<size_t>(s.nself) * s.Z);
+    if (!v.chk_shared) {
+      *off_s = static_cast<long long>(f);
+      f += align64(s.M);
+    }
+  } else if (v.alg == ALG_CBP_NMS && !v.chk_shared) {
+    f += align64(2 * static_cast<size_t>(s.M));
   }
-  return (f + 63) & ~static_cast<size_t>(63);  // 256-byte aligned slots
+  return f;  // multiple of 64 floats: 256-byte aligned slots
 }
 
 }  // namespace cbp
@@ -144,7 +156,11 @@ using namespace cbp;
 struct cbp_code {
   int dev = 0;
   int mb = 0, nb = 0, Z = 0, N = 0, M = 0, E = 0, K = -1, nnzb = 0, maxdeg = 0;
+  int ncomp = 0, nself = 0;  // columns of weight >= 2 / of weight 1
   CodeDev d;
+  Shape shape() const {
+    return Shape{Z, N, M, E, nnzb, mb, nb, (N + 31) / 32, ncomp, nself};
+  }
 };
 
 namespace {
@@ -187,86 +203,87 @@ int gf2_rank(const int32_t* base, int mb, int nb, int Z) {
 }
 
 struct Plan {
-  Variant v;
+  Variant v{};
   int F = 0, threads = 0, grid = 0;
   size_t smem = 0;
-  long long ws_slot = 0;
+  long long ws_slot = 0, ws_off_sv = 0, ws_off_s = 0;
   int sh_frame = 0;
   size_t ws_bytes = 0;
 };
 
+// Launch plan: for each layout variant the number of frame slots per CTA that gives
+// the most resident warps per SM; the variant with the most warps wins (ties: the
+// earlier, i.e. more shared-memory-resident, variant).  CBP_PLAN_CHK=0/1 in the
+// environment restricts the check-state placement (tuning experiments).
 int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan* out) {
   std::vector<Variant> cands;
   switch (alg) {
     case ALG_CBP_SP:
-      cands = {{ALG_CBP_SP, true, true}, {ALG_CBP_SP, false, true}, {ALG_CBP_SP, false, false}};
+      cands = {{ALG_CBP_SP, true}, {ALG_CBP_SP, false}};
       break;
     case ALG_CBP_NMS:
-      cands = {{ALG_CBP_NMS, false, true}, {ALG_CBP_NMS, false, false}};
+      cands = {{ALG_CBP_NMS, true}, {ALG_CBP_NMS, false}};
       break;
     case ALG_LBP_NMS:
       if (c->maxdeg > kMaxDeg) return CBP_EUNSUPPORTED;
-      cands = {{ALG_LBP_NMS, false, true}};
+      cands = {{ALG_LBP_NMS, true}};
       break;
     case ALG_FBP_SP:
       if (c->maxdeg > kMaxDeg) return CBP_EUNSUPPORTED;
-      cands = {{ALG_FBP_SP, false, false}};
+      cands = {{ALG_FBP_SP, false}};
       break;
     default:
       return CBP_EINVAL;
   }
-  const int words = (c->N + 31) / 32;
+  if (const char* e = std::getenv("CBP_PLAN_CHK")) {
+    if (alg == ALG_CBP_SP || alg == ALG_CBP_NMS) {
+      const bool want = e[0] == '1';
+      cands.erase(std::remove_if(cands.begin(), cands.end(),
+                                 [&](const Variant& v) { return v.chk_shared != want; }),
+                  cands.end());
+    }
+  }
+  const Shape sh = c->shape();
   bool found = false;
   Plan best;
-  int best_warps = -1;
+  int best_warps = -1, best_ctas = 0;
   for (const Variant& v : cands) {
     cudaFuncAttributes fa;
     if (decoder_func_attrs(v, &fa) != cudaSuccess) return CBP_ECUDA;
     const int fmax = fa.maxThreadsPerBlock / c->Z;
-    if (fmax < 1) continue;
-    const size_t fr_floats = shared_frame_floats(v, c->N, c->M, words);
-    Plan pv;
-    int pv_warps = -1;
+    const size_t fr_floats = shared_frame_floats(v, sh);
     for (int F = 1; F <= fmax; ++F) {
-      const size_t smem = shared_fixed_bytes(v, c->nnzb, c->mb, c->nb, F) + F * fr_floats * 4;
+      const size_t smem = shared_fixed_bytes(v, sh, F) + F * fr_floats * 4;
       if (smem > static_cast<size_t>(di.smem_optin)) break;
       const int threads = (F * c->Z + 31) / 32 * 32;
       if (threads > fa.maxThreadsPerBlock) break;
       int ctas = 0;
       if (decoder_occupancy(v, threads, smem, &ctas) != cudaSuccess) return CBP_ECUDA;
       const int warps = ctas * threads / 32;
-      if (ctas >= 1 && warps >= pv_warps) {
-        pv_warps = warps;
-        pv.v = v;
-        pv.F = F;
-        pv.threads = threads;
-        pv.smem = smem;
-        pv.sh_frame = static_cast<int>(fr_floats);
-        pv.grid = ctas;  // CTAs per SM for now
+      if (ctas >= 1 && warps > best_warps) {
+        best_warps = warps;
+        best_ctas = ctas;
+        best.v = v;
+        best.F = F;
+        best.threads = threads;
+        best.smem = smem;
+        best.sh_frame = static_cast<int>(fr_floats);
+        found = true;
       }
     }
-    if (pv_warps < 0) continue;
-    // first feasible candidate with at least 8 resident warps per SM wins
-    if (!found || (best_warps < 8 && pv_warps > best_warps)) {
-      best = pv;
-      best_warps = pv_warps;
-      found = true;
-    }
-    if (best_warps >= 8) break;
   }
   if (!found) return CBP_EUNSUPPORTED;
-  const int ctas_per_sm = best.grid;
   // small batches: fewer frames per CTA so the frames spread over the SMs
   const int spread = std::max(1, (batch + di.sms - 1) / di.sms);
   if (best.F > spread) {
     best.F = spread;
     best.threads = (best.F * c->Z + 31) / 32 * 32;
-    best.smem = shared_fixed_bytes(best.v, c->nnzb, c->mb, c->nb, best.F) +
+    best.smem = shared_fixed_bytes(best.v, sh, best.F) +
                 best.F * static_cast<size_t>(best.sh_frame) * 4;
   }
   const long long need = (static_cast<long long>(batch) + best.F - 1) / best.F;
-  best.grid = static_cast<int>(std::max(1LL, std::min<long long>(need, 1LL * di.sms * ctas_per_sm)));
-  best.ws_slot = static_cast<long long>(ws_slot_floats(best.v, c->N, c->M, c->E));
+  best.grid = static_cast<int>(std::max(1LL, std::min<long long>(need, 1LL * di.sms * best_ctas)));
+  best.ws_slot = static_cast<long long>(ws_slot_floats(best.v, sh, &best.ws_off_sv, &best.ws_off_s));
   best.ws_bytes = static_cast<size_t>(best.grid) * best.F * best.ws_slot * sizeof(float);
   *out = best;
   return CBP_OK;
@@ -334,11 +351,13 @@ int cbp_code_create(const int32_t* base, int mb, int nb, int Z, cbp_code_t** out
   }
   std::vector<ColEntry> cols;
   std::vector<int> cptr(1, 0);
+  int ncomp = 0, nself = 0;
   for (int c = 0; c < nb; ++c) {
     std::vector<int> rows;
     for (int r = 0; r < mb; ++r)
       if (base[r * nb + c] >= 0) rows.push_back(r);
     const int w = static_cast<int>(rows.size());
+    const uint32_t kind_idx = static_cast<uint32_t>(w == 1 ? nself++ : ncomp++);
     for (int k = 0; k < w; ++k) {
       const int r = rows[k], pr = rows[(k + w - 1) % w];
       BaseEdge& e = edges[idx[r * nb + c]];
@@ -346,6 +365,7 @@ int cbp_code_create(const int32_t* base, int mb, int nb, int Z, cbp_code_t** out
       e.ps = static_cast<uint16_t>(base[pr * nb + c]);
       e.pe = static_cast<uint16_t>(idx[pr * nb + c]);
       e.flags = static_cast<uint16_t>((k == 0 ? kFirst : 0) | (w == 1 ? kSelf : 0));
+      e.pad = kind_idx;
       ColEntry ce{};
       ce.r = static_cast<uint16_t>(r);
       ce.s = static_cast<uint16_t>(base[r * nb + c]);
@@ -366,6 +386,8 @@ int cbp_code_create(const int32_t* base, int mb, int nb, int Z, cbp_code_t** out
   c->nnzb = nnzb;
   c->E = nnzb * Z;
   c->maxdeg = maxdeg;
+  c->ncomp = ncomp;
+  c->nself = nself;
   // K = N - rank(H): full rank when the parity part is block lower-triangular with
   // an identity-shift diagonal in column (nb - mb + r); else eliminate small codes.
   bool tri = nb > mb;
@@ -488,7 +510,11 @@ int cbp_decode_ex(const cbp_code_t* c, const float* llr, uint32_t* hard_out, int
   p.F = pl.F;
   p.slots = pl.grid * pl.F;
   p.maxdeg = c->maxdeg;
+  p.ncomp = c->ncomp;
+  p.nself = c->nself;
   p.ws_slot = pl.ws_slot;
+  p.ws_off_sv = pl.ws_off_sv;
+  p.ws_off_s = pl.ws_off_s;
   p.sh_frame = pl.sh_frame;
   cudaError_t e = launch_decoder(pl.v, p, pl.grid, pl.threads, pl.smem,
                                  reinterpret_cast<cudaStream_t>(stream));

@@ -52,7 +52,8 @@ struct BaseEdge {
   uint16_t ps;     // shift of the predecessor entry
   uint16_t pe;     // index of the predecessor entry in this list
   uint16_t flags;  // kFirst: r is the first row of column c; kSelf: c has weight 1
-  uint32_t pad;
+  uint32_t pad;    // low 16 bits: index of column c among the columns of its kind
+                   // (weight >= 2 columns, or weight-1 columns)
 };
 constexpr uint16_t kFirst = 1, kSelf = 2;
 
@@ -87,7 +88,10 @@ struct KParams {
   int F;                 // frames per CTA
   int slots;             // gridDim.x * F
   int maxdeg;
+  int ncomp, nself;      // columns of weight >= 2 / of weight 1
   long long ws_slot;     // floats of workspace per frame slot
+  long long ws_off_sv;   // CBP-SP: offset (floats) of the weight-1 (Q*, phi) pairs
+  long long ws_off_s;    // CBP-SP: offset of the check-beliefs when not shared
   int sh_frame;          // floats of shared memory per frame
 };
 
@@ -95,14 +99,17 @@ enum Alg { ALG_CBP_SP = 0, ALG_CBP_NMS = 1, ALG_LBP_NMS = 2, ALG_FBP_SP = 3 };
 
 struct Variant {
   int alg;
-  bool phi_cache;   // keep phi(|Q*|) per variable in shared memory (CBP-SP)
   bool chk_shared;  // check state in shared memory (else in the workspace)
 };
 
-// Shared-memory and workspace layout of one launch.
-size_t shared_fixed_bytes(const Variant& v, int nnzb, int mb, int nb, int F);
-size_t shared_frame_floats(const Variant& v, int N, int M, int words);
-size_t ws_slot_floats(const Variant& v, int N, int M, int E);
+// Sizes that fix the shared-memory and workspace layout of a launch.
+struct Shape {
+  int Z, N, M, E, nnzb, mb, nb, words, ncomp, nself;
+};
+size_t shared_fixed_bytes(const Variant& v, const Shape& s, int F);
+size_t shared_frame_floats(const Variant& v, const Shape& s);
+// workspace floats per slot; *off_sv, *off_s receive the CBP-SP offsets
+size_t ws_slot_floats(const Variant& v, const Shape& s, long long* off_sv, long long* off_s);
 
 // Launchers (cbp_layered.cu / cbp_flood.cu).
 cudaError_t launch_decoder(const Variant& v, const KParams& p, int grid, int threads,
@@ -110,6 +117,8 @@ cudaError_t launch_decoder(const Variant& v, const KParams& p, int grid, int thr
 cudaError_t decoder_func_attrs(const Variant& v, cudaFuncAttributes* a);
 cudaError_t decoder_set_smem(const Variant& v, int bytes);
 cudaError_t decoder_occupancy(const Variant& v, int threads, size_t smem, int* ctas);
+void* sp_kernel_ptr(bool chk_shared);  // cbp_sp.cu
+void* flood_kernel_ptr();              // cbp_flood.cu
 cudaError_t launch_phi(const float* x, float* y, long long n, const float4* tab, float xlo,
                        cudaStream_t st);
 

@@ -1,5 +1,5 @@
-// Sequential-schedule decoders on sm_103a: CBP (log-tanh and normalized min-sum)
-// and the layered normalized min-sum comparator.
+// Sequential-schedule decoders on sm_103a: CBP normalized min-sum and the layered
+// normalized min-sum comparator (CBP in log-tanh form has its own kernel, cbp_sp.cu).
 //
 // Parallel layout.  A CTA holds F frame slots of Z lanes each.  The checks of one
 // base row r (m = r*Z + i, i = 0..Z-1) share no variable: every base column is a
@@ -10,8 +10,8 @@
 // the next one (slot g of the launch decodes frames g, g + slots, g + 2 slots, ...).
 //
 // Per frame slot:
-//   shared:    Q*_v (N), optionally phi(|Q*_v|) (N), the check state (M or 2M),
-//              hard-decision bits (ceil(N/32) words)
+//   shared:    Q*_v (CBP) or Lambda_v (LBP) (N), the CBP check state (min1 with the
+//              sign of Omega, min2: 2M) when it fits, hard-decision bits (ceil(N/32) words)
 //   workspace: the C2V messages R (E floats, [base entry][lane]), and the check
 //              state when it does not fit in shared memory.
 // The C2V message of edge (c_j, v) is produced when v is visited by the next check
@@ -40,49 +40,11 @@ struct Ctx {
   int t;                       // current sweep (1-based)
   const BaseEdge* __restrict__ e;
   float* __restrict__ Q;       // Q*_v (CBP) or Lambda_v (LBP), shared
-  float* __restrict__ P;       // phi(|Q*_v|), shared (CBP-SP with the cache)
-  float* __restrict__ C0;      // check state 0: signed S (CBP-SP) or signed min1 (CBP-NMS)
+  float* __restrict__ C0;      // check state 0: signed min1 (CBP-NMS)
   float* __restrict__ C1;      // check state 1: min2 (CBP-NMS)
   float* __restrict__ R;       // C2V messages of this slot, global
-  const float4* __restrict__ tab;
-  float xlo, alpha;
+  float alpha;
 };
-
-// CBP, log-tanh form: Step 2 (1) a)-e) for the edges of check (r, z), then Eq. (s4e23).
-template <bool PHC>
-__device__ __forceinline__ void cbp_sp_check(const Ctx& x, int r, int k0, int k1, int z) {
-  const int Z = x.Z;
-  float Sacc = 0.0f;
-  uint32_t sig = 0;
-  for (int k = k0; k < k1; ++k) {
-    const BaseEdge be = x.e[k];
-    const int zv = mod_add(z + be.s, Z);
-    const int v = be.c * Z + zv;
-    const bool self = be.flags & kSelf;
-    const float Rold0 = (x.t > 1 && !self) ? x.R[k * Z + z] : 0.0f;
-    const float q = x.Q[v];
-    float Rn = 0.0f;
-    if (!(x.t == 1 && (be.flags & kFirst))) {
-      // a) c_j = predecessor check holding v;  b) B2V, Eqs. (s4e18), (s4e13)
-      int zj = zv - be.ps;
-      zj = zj < 0 ? zj + Z : zj;
-      const float Sj = x.C0[be.pr * Z + zj];
-      const float ph = PHC ? x.P[v] : phi_eval(fabsf(q), x.xlo, x.tab);
-      const float mag = phi_eval(fabsf(__fsub_rn(fabsf(Sj), ph)), x.xlo, x.tab);
-      Rn = (sign_bit(Sj) ^ (q < 0.0f)) ? -mag : mag;
-      x.R[be.pe * Z + zj] = Rn;               // e) R_{c_j->v} <- R^new
-    }
-    const float Rold = self ? Rn : Rold0;     // weight-1 column: c_j == c_i
-    const float lam = __fadd_rn(q, Rn);       // c) Eq. (s4e20)
-    const float qn = __fsub_rn(lam, Rold);    //    Eq. (s4e19)
-    const float phn = phi_eval(fabsf(qn), x.xlo, x.tab);
-    Sacc = __fadd_rn(Sacc, phn);              // d) C2B, Eq. (s4e21) as a sum of phi
-    sig ^= (qn < 0.0f);
-    x.Q[v] = qn;                              // e) Q_{v->c*} <- Q^new
-    if (PHC) x.P[v] = phn;
-  }
-  x.C0[r * Z + z] = sig ? -Sacc : Sacc;       // Eq. (s4e23); the sign bit carries sgn(Omega)
-}
 
 // CBP normalized min-sum, Eqs. (s4e18xx), (s4e21xx).
 __device__ __forceinline__ void cbp_nms_check(const Ctx& x, int r, int k0, int k1, int z) {
@@ -166,32 +128,23 @@ __device__ __forceinline__ void lbp_nms_check(const Ctx& x, int r, int k0, int k
   (void)r;
 }
 
-// Flushed posterior of variable v (CBP), a read-only evaluation of Eq. (s4e20) with
-// the last check of the sweep holding v as c_j.
-template <int ALG, bool PHC>
+// Flushed posterior of variable v (CBP min-sum), a read-only evaluation of Eq. (s4e20)
+// with the last check of the sweep holding v as c_j.
 __device__ __forceinline__ float cbp_flush(const Ctx& x, int v, int ci) {
   const float q = x.Q[v];
-  if (ALG == ALG_CBP_SP) {
-    const float Sj = x.C0[ci];
-    const float ph = PHC ? x.P[v] : phi_eval(fabsf(q), x.xlo, x.tab);
-    const float mag = phi_eval(fabsf(__fsub_rn(fabsf(Sj), ph)), x.xlo, x.tab);
-    return __fadd_rn(q, (sign_bit(Sj) ^ (q < 0.0f)) ? -mag : mag);
-  } else {
-    const float a1 = x.C0[ci];
-    const float b1 = fabsf(a1);
-    const float mag = (fabsf(q) == b1) ? x.C1[ci] : b1;
-    const float rm = __fmul_rn(x.alpha, mag);
-    return __fadd_rn(q, (sign_bit(a1) ^ (q < 0.0f)) ? -rm : rm);
-  }
+  const float a1 = x.C0[ci];
+  const float b1 = fabsf(a1);
+  const float mag = (fabsf(q) == b1) ? x.C1[ci] : b1;
+  const float rm = __fmul_rn(x.alpha, mag);
+  return __fadd_rn(q, (sign_bit(a1) ^ (q < 0.0f)) ? -rm : rm);
 }
 
 // ---------------------------------------------------------------------------
 // The kernel.
 // ---------------------------------------------------------------------------
-template <int ALG, bool PHC, bool CHKS>
+template <int ALG, bool CHKS>
 __global__ void __launch_bounds__(1024, 1) layered_kernel(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr bool kSP = (ALG == ALG_CBP_SP);
   constexpr bool kLBP = (ALG == ALG_LBP_NMS);
   const int Z = p.Z, N = p.N, M = p.M, words = p.words, F = p.F;
   const int tid = threadIdx.x;
@@ -201,8 +154,6 @@ __global__ void __launch_bounds__(1024, 1) layered_kernel(const KParams p) {
 
   // ---- shared-memory carve-up (must match shared_fixed_bytes / shared_frame_floats)
   unsigned char* sp = smem;
-  float4* s_tab = reinterpret_cast<float4*>(sp);
-  if (kSP) sp += sizeof(float4) * kPhiSegments;
   BaseEdge* s_e = reinterpret_cast<BaseEdge*>(sp);
   sp += sizeof(BaseEdge) * p.nnzb;
   int* s_rptr = reinterpret_cast<int*>(sp);
@@ -219,30 +170,21 @@ __global__ void __launch_bounds__(1024, 1) layered_kernel(const KParams p) {
     const ColEntry ce = p.cols[p.cptr[c + 1] - 1];   // last row of column c
     s_last[c] = (uint32_t(ce.r) << 16) | ce.s;
   }
-  if (kSP)
-    for (int i = tid; i < kPhiSegments; i += blockDim.x) s_tab[i] = p.phi_tab[i];
   if (tid < F) {
     s_slot[tid].frame = blockIdx.x * F + tid;
     s_slot[tid].t = 0;
     s_slot[tid].unsat = 0;
   }
 
-  // per-frame shared arrays: Q [N] | P [N] (PHC) | C0 [M] | C1 [M] (NMS) | bits [words]
+  // per-frame shared arrays: Q [N] | C0 [M] | C1 [M] (CBP-NMS, CHKS) | bits [words]
   const int Npad = (N + 3) & ~3, Mpad = (M + 3) & ~3;
   float* base = s_frames + static_cast<size_t>(lane ? f : 0) * p.sh_frame;
   Ctx x;
   x.Z = Z;
   x.e = s_e;
-  x.tab = s_tab;
-  x.xlo = p.phi_xlo;
   x.alpha = p.alpha;
   x.Q = base;
   float* nxt = base + Npad;
-  x.P = nullptr;
-  if (PHC) {
-    x.P = nxt;
-    nxt += Npad;
-  }
   const long long g = static_cast<long long>(blockIdx.x) * F + (lane ? f : 0);
   float* wsl = p.ws + g * p.ws_slot;
   x.R = wsl;
@@ -250,14 +192,11 @@ __global__ void __launch_bounds__(1024, 1) layered_kernel(const KParams p) {
   if (!kLBP) {
     if (CHKS) {
       x.C0 = nxt;
-      nxt += Mpad;
-      if (!kSP) {
-        x.C1 = nxt;
-        nxt += Mpad;
-      }
+      x.C1 = nxt + Mpad;
+      nxt += 2 * Mpad;
     } else {
       x.C0 = wsl + p.E;
-      if (!kSP) x.C1 = wsl + p.E + M;
+      x.C1 = wsl + p.E + M;
     }
   }
   uint32_t* bits = reinterpret_cast<uint32_t*>(nxt);
@@ -285,8 +224,7 @@ __global__ void __launch_bounds__(1024, 1) layered_kernel(const KParams p) {
     for (int r = 0; r < p.mb; ++r) {
       if (act) {
         const int k0 = s_rptr[r], k1 = s_rptr[r + 1];
-        if (ALG == ALG_CBP_SP) cbp_sp_check<PHC>(x, r, k0, k1, z);
-        else if (ALG == ALG_CBP_NMS) cbp_nms_check(x, r, k0, k1, z);
+        if (ALG == ALG_CBP_NMS) cbp_nms_check(x, r, k0, k1, z);
         else lbp_nms_check(x, r, k0, k1, z);
       }
       __syncthreads();
@@ -308,7 +246,7 @@ __global__ void __launch_bounds__(1024, 1) layered_kernel(const KParams p) {
           const uint32_t l = s_last[c];
           int zk = z - int(l & 0xffffu);
           zk = zk < 0 ? zk + Z : zk;
-          lb = cbp_flush<ALG, PHC>(x, v, int(l >> 16) * Z + zk);
+          lb = cbp_flush(x, v, int(l >> 16) * Z + zk);
         }
         if (lb < 0.0f) atomicOr(bits + (v >> 5), 1u << (v & 31));
         if (so) so[v] = lb;
@@ -354,33 +292,22 @@ __global__ void __launch_bounds__(1024, 1) layered_kernel(const KParams p) {
   }
 }
 
-template <int ALG, bool PHC, bool CHKS>
+template <int ALG, bool CHKS>
 void* kernel_ptr() {
-  return reinterpret_cast<void*>(&layered_kernel<ALG, PHC, CHKS>);
-}
-
-void* select_layered(const Variant& v) {
-  switch (v.alg) {
-    case ALG_CBP_SP:
-      if (v.phi_cache) return v.chk_shared ? kernel_ptr<ALG_CBP_SP, true, true>()
-                                           : kernel_ptr<ALG_CBP_SP, true, false>();
-      return v.chk_shared ? kernel_ptr<ALG_CBP_SP, false, true>()
-                          : kernel_ptr<ALG_CBP_SP, false, false>();
-    case ALG_CBP_NMS:
-      return v.chk_shared ? kernel_ptr<ALG_CBP_NMS, false, true>()
-                          : kernel_ptr<ALG_CBP_NMS, false, false>();
-    case ALG_LBP_NMS:
-      return kernel_ptr<ALG_LBP_NMS, false, true>();
-  }
-  return nullptr;
+  return reinterpret_cast<void*>(&layered_kernel<ALG, CHKS>);
 }
 
 }  // namespace
 
-void* flood_kernel_ptr();  // cbp_flood.cu
-
 static void* select_kernel(const Variant& v) {
-  return v.alg == ALG_FBP_SP ? flood_kernel_ptr() : select_layered(v);
+  switch (v.alg) {
+    case ALG_CBP_SP: return sp_kernel_ptr(v.chk_shared);
+    case ALG_CBP_NMS:
+      return v.chk_shared ? kernel_ptr<ALG_CBP_NMS, true>() : kernel_ptr<ALG_CBP_NMS, false>();
+    case ALG_LBP_NMS: return kernel_ptr<ALG_LBP_NMS, true>();
+    case ALG_FBP_SP: return flood_kernel_ptr();
+  }
+  return nullptr;
 }
 
 cudaError_t decoder_func_attrs(const Variant& v, cudaFuncAttributes* a) {
