@@ -121,6 +121,32 @@ int cbp_decode_ex(const cbp_code_t* code, const float* llr, uint32_t* hard_out,
                   int32_t* iters_out, int max_iter, int batch, void* workspace,
                   size_t workspace_bytes, cbp_stream_t stream, const cbp_opts_t* opts);
 
+/* Size of the decoder scratch array compiled into the library for cbp_decode_noalloc. */
+#define CBP_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* cbp_decode for callers that cannot allocate device memory.  (The paper has no
+ * counterpart: this is a deployment convenience of the library.)
+ *
+ * Some callers cannot call cudaMalloc or hand over a workspace: code running where an
+ * allocation could fail or block at the wrong moment (a real-time receive loop, a
+ * plugin inside a host application that owns all device memory), or a caller that has
+ * no allocator at all.  This entry point decodes exactly like cbp_decode (CBP log-tanh
+ * form, syndrome stop) but keeps its scratch in a fixed array of
+ * CBP_NOALLOC_SCRATCH_BYTES that is part of the library's device image; every GPU on
+ * which the library's kernels are loaded holds that array until the process exits.
+ * The caller still passes the inputs and outputs (same layout as cbp_decode); the call
+ * allocates nothing.
+ *   - Larger batches run with fewer frame slots in flight, so they fit the array; a code
+ *     whose single frame slot needs more than the array returns CBP_EWORKSPACE.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the previous call's contents (the
+ *     decoder writes every scratch value before reading it, so nothing needs clearing).
+ *     Calls whose executions overlap on the GPU — different streams, or different host
+ *     threads without ordering — race on the array: serialise them. */
+int cbp_decode_noalloc(const cbp_code_t* code, const float* llr, uint32_t* hard_out,
+                       int32_t* iters_out, int max_iter, int batch, cbp_stream_t stream);
+
 /* Evaluate the library's phi (Eq. s2e5, the clamped FP32 form used by the decoders)
  * on n device values: y[i] = phi(x[i]).  x, y device, 4-byte aligned, n >= 0. */
 int cbp_phi(const float* x, float* y, int64_t n, cbp_stream_t stream);

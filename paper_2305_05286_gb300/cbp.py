@@ -24,7 +24,7 @@ STATUS = {0: "CBP_OK", -1: "CBP_EINVAL", -2: "CBP_ENOMEM", -3: "CBP_ECUDA",
 
 # Every symbol include/cbp.h declares (checked by the ABI test).
 EXPORTS = ("cbp_code_create", "cbp_code_destroy", "cbp_code_info", "cbp_workspace_bytes",
-           "cbp_decode", "cbp_decode_ex", "cbp_phi", "cbp_strerror")
+           "cbp_decode", "cbp_decode_ex", "cbp_decode_noalloc", "cbp_phi", "cbp_strerror")
 
 
 class CbpError(RuntimeError):
@@ -63,6 +63,8 @@ def lib(build_if_needed: bool = True):
             L.cbp_decode.argtypes = [P, P, P, P, I, I, P, Z, P]
             L.cbp_decode_ex.restype = I
             L.cbp_decode_ex.argtypes = [P, P, P, P, I, I, P, Z, P, C.POINTER(_Opts)]
+            L.cbp_decode_noalloc.restype = I
+            L.cbp_decode_noalloc.argtypes = [P, P, P, P, I, I, P]
             L.cbp_phi.restype = I
             L.cbp_phi.argtypes = [P, P, C.c_int64, P]
             L.cbp_strerror.restype = C.c_char_p

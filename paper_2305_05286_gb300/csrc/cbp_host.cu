@@ -528,6 +528,95 @@ int cbp_decode(const cbp_code_t* c, const float* llr, uint32_t* hard_out, int32_
                        workspace_bytes, stream, nullptr);
 }
 
+// ---------------------------------------------------------------------------
+// cbp_decode_noalloc: the decoder scratch in a fixed device array of this file.
+// Host code never dereferences g_noalloc_scratch (its name is a host-side stand-in);
+// the device address is looked up once per device and passed to the kernel.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[CBP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+int noalloc_scratch(int dev, void** out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return CBP_ECUDA;
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return CBP_OK;
+}
+}  // namespace
+
+int cbp_decode_noalloc(const cbp_code_t* c, const float* llr, uint32_t* hard_out,
+                       int32_t* iters_out, int max_iter, int batch, cbp_stream_t stream) {
+  if (!c || max_iter < 1 || batch < 0) return CBP_EINVAL;
+  if (batch == 0) return CBP_OK;
+  if (!llr || !hard_out || !iters_out) return CBP_EINVAL;
+  if (!aligned(llr, 16) || !aligned(hard_out, 4) || !aligned(iters_out, 4)) return CBP_EINVAL;
+  DeviceInfo* di = nullptr;
+  int dev = 0;
+  if (int rc = current_device(&di, &dev)) return rc;
+  if (dev != c->dev) return CBP_EDEVICE;
+  void* scratch = nullptr;
+  if (int rc = noalloc_scratch(dev, &scratch)) return rc;
+  Plan pl;
+  if (int rc = make_plan(c, *di, ALG_CBP_SP, batch, &pl)) return rc;
+  // Fit the launch into the array: fewer CTAs, and if one CTA is still too big, fewer
+  // frame slots per CTA.  Slots loop over frames, so any grid decodes the whole batch.
+  const size_t cap = CBP_NOALLOC_SCRATCH_BYTES;
+  const size_t slot_bytes = static_cast<size_t>(pl.ws_slot) * sizeof(float);
+  if (slot_bytes > cap) return CBP_EWORKSPACE;
+  if (static_cast<size_t>(pl.F) * slot_bytes > cap) {
+    pl.F = static_cast<int>(cap / slot_bytes);
+    pl.threads = (pl.F * c->Z + 31) / 32 * 32;
+    pl.smem = shared_fixed_bytes(pl.v, c->shape(), pl.F) +
+              static_cast<size_t>(pl.F) * pl.sh_frame * sizeof(float);
+  }
+  const long long max_grid = static_cast<long long>(cap / (pl.F * slot_bytes));
+  pl.grid = static_cast<int>(std::min<long long>(pl.grid, max_grid));
+  pl.ws_bytes = static_cast<size_t>(pl.grid) * pl.F * slot_bytes;
+
+  KParams p{};
+  p.llr = llr;
+  p.hard = hard_out;
+  p.iters = iters_out;
+  p.soft = nullptr;
+  p.ws = static_cast<float*>(scratch);
+  p.edges = c->d.edges;
+  p.rptr = c->d.rptr;
+  p.cols = c->d.cols;
+  p.cptr = c->d.cptr;
+  p.phi_tab = di->tab;
+  p.phi_xlo = di->xlo;
+  p.Z = c->Z;
+  p.mb = c->mb;
+  p.nb = c->nb;
+  p.nnzb = c->nnzb;
+  p.N = c->N;
+  p.M = c->M;
+  p.E = c->E;
+  p.words = (c->N + 31) / 32;
+  p.batch = batch;
+  p.max_iter = max_iter;
+  p.stop = CBP_STOP_SYNDROME;
+  p.alpha = 0.75f;
+  p.F = pl.F;
+  p.slots = pl.grid * pl.F;
+  p.maxdeg = c->maxdeg;
+  p.ncomp = c->ncomp;
+  p.nself = c->nself;
+  p.ws_slot = pl.ws_slot;
+  p.ws_off_sv = pl.ws_off_sv;
+  p.ws_off_s = pl.ws_off_s;
+  p.sh_frame = pl.sh_frame;
+  cudaError_t e = launch_decoder(pl.v, p, pl.grid, pl.threads, pl.smem,
+                                 reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? CBP_OK : CBP_ECUDA;
+}
+
 int cbp_phi(const float* x, float* y, int64_t n, cbp_stream_t stream) {
   if (n < 0) return CBP_EINVAL;
   if (n == 0) return CBP_OK;
