@@ -79,8 +79,11 @@ int device_init(int dev, DeviceInfo** out) {
         cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
             cudaSuccess)
       return CBP_ECUDA;
-    const Variant all[] = {{ALG_CBP_SP, true},   {ALG_CBP_SP, false}, {ALG_CBP_NMS, true},
-                           {ALG_CBP_NMS, false}, {ALG_LBP_NMS, true}, {ALG_FBP_SP, false}};
+    const Variant all[] = {{ALG_CBP_SP, true, 1},  {ALG_CBP_SP, false, 1},
+                           {ALG_CBP_SP, true, 2},  {ALG_CBP_SP, false, 2},
+                           {ALG_CBP_SP, true, 1, true}, {ALG_CBP_SP, false, 1, true},
+                           {ALG_CBP_NMS, true, 1}, {ALG_CBP_NMS, false, 1},
+                           {ALG_LBP_NMS, false, 1}, {ALG_FBP_SP, false, 1}};
     for (const Variant& v : all)
       if (decoder_set_smem(v, d.smem_optin) != cudaSuccess) return CBP_ECUDA;
     d.tab = static_cast<float4*>(addr);
@@ -105,8 +108,9 @@ size_t align4(size_t n) { return (n + 3) & ~static_cast<size_t>(3); }
 size_t align64(size_t n) { return (n + 63) & ~static_cast<size_t>(63); }
 }  // namespace
 
-size_t shared_fixed_bytes(const Variant& v, const Shape& s, int F) {
-  size_t b = sizeof(BaseEdge) * s.nnzb + sizeof(int) * align4(s.mb + 1) + 12 * align4(F);
+size_t shared_fixed_bytes(const Variant& v, const Shape& s, int groups) {
+  size_t b = sizeof(BaseEdge) * s.nnzb + sizeof(int) * align4(s.mb + 1) +
+             12 * align4(static_cast<size_t>(groups) * v.fpt);
   switch (v.alg) {
     case ALG_CBP_SP:
       b += sizeof(float4) * kPhiSegments + sizeof(uint2) * ((s.nb + 1) & ~1);
@@ -115,8 +119,8 @@ size_t shared_fixed_bytes(const Variant& v, const Shape& s, int F) {
       b += sizeof(float4) * kPhiSegments + sizeof(ColEntry) * ((s.nnzb + 1) & ~1) +
            sizeof(int) * align4(s.nb + 1);
       break;
-    default:
-      b += sizeof(uint32_t) * align4(s.nb);
+    default:  // min-sum kernels
+      b += sizeof(uint2) * ((s.nb + 1) & ~1);
   }
   return b;
 }
@@ -125,28 +129,46 @@ size_t shared_frame_floats(const Variant& v, const Shape& s) {
   const size_t W = align4(s.words);
   switch (v.alg) {
     case ALG_CBP_SP:
-      return 2 * static_cast<size_t>(s.ncomp) * s.Z + (v.chk_shared ? align4(s.M) : 0) + W;
+      return v.fpt * (2 * static_cast<size_t>(s.ncomp) * s.Z + (v.chk_shared ? align4(s.M) : 0) + W);
     case ALG_CBP_NMS:
-      return align4(s.N) + (v.chk_shared ? 2 * align4(s.M) : 0) + W;
-    default:
+      return align4(static_cast<size_t>(s.ncomp) * s.Z) +
+             (v.chk_shared ? 2 * static_cast<size_t>((s.M + 1) & ~1) : 0) + W;
+    case ALG_LBP_NMS:
+      return align4(static_cast<size_t>(s.ncomp) * s.Z) + W;
+    default:  // flooding: Lambda [N] | bits
       return align4(s.N) + W;
   }
 }
 
-size_t ws_slot_floats(const Variant& v, const Shape& s, long long* off_sv, long long* off_s) {
-  size_t f = align64(s.E);
-  *off_sv = *off_s = 0;
-  if (v.alg == ALG_CBP_SP) {
-    *off_sv = static_cast<long long>(f);
-    f += align64(2 * static_cast<size_t>(s.nself) * s.Z);
-    if (!v.chk_shared) {
-      *off_s = static_cast<long long>(f);
-      f += align64(s.M);
-    }
-  } else if (v.alg == ALG_CBP_NMS && !v.chk_shared) {
-    f += align64(2 * static_cast<size_t>(s.M));
+WsLayout ws_layout(const Variant& v, const Shape& s) {
+  WsLayout w;
+  size_t f = 0;
+  switch (v.alg) {
+    case ALG_CBP_SP:  // R [E][fpt] | (Q*, phi) of weight-1 columns | S (not shared)
+      f = align64(static_cast<size_t>(s.E) * v.fpt);
+      w.off_sv = static_cast<long long>(f);
+      f += align64(2 * static_cast<size_t>(v.fpt) * s.nself * s.Z);
+      if (!v.chk_shared) {
+        w.off_s = static_cast<long long>(f);
+        f += align64(static_cast<size_t>(v.fpt) * s.M);
+      }
+      break;
+    case ALG_CBP_NMS:
+    case ALG_LBP_NMS:  // weight-1 column state | per-check state (uint4) | CBP (min1, min2)
+      w.off_sv = 0;
+      f = align64(static_cast<size_t>(s.nself) * s.Z);
+      w.off_s = static_cast<long long>(f);
+      f += align64(4 * static_cast<size_t>(s.M));
+      if (v.alg == ALG_CBP_NMS && !v.chk_shared) {
+        w.off_c = static_cast<long long>(f);
+        f += align64(2 * static_cast<size_t>(s.M));
+      }
+      break;
+    default:  // flooding: R [E]
+      f = align64(s.E);
   }
-  return f;  // multiple of 64 floats: 256-byte aligned slots
+  w.slot = static_cast<long long>(f);  // multiple of 64 floats: 256-byte aligned groups
+  return w;
 }
 
 }  // namespace cbp
@@ -203,30 +225,50 @@ int gf2_rank(const int32_t* base, int mb, int nb, int Z) {
 }
 
 struct Plan {
-  Variant v{};
+  Variant v{};  // F below counts lane groups; a group decodes v.fpt frames
   int F = 0, threads = 0, grid = 0;
+  int team_groups = 0;  // lane groups per team (CBP-SP); >= F means one team
   size_t smem = 0;
-  long long ws_slot = 0, ws_off_sv = 0, ws_off_s = 0;
+  WsLayout ws{};
   int sh_frame = 0;
   size_t ws_bytes = 0;
 };
 
-// Launch plan: for each layout variant the number of frame slots per CTA that gives
-// the most resident warps per SM; the variant with the most warps wins (ties: the
-// earlier, i.e. more shared-memory-resident, variant).  CBP_PLAN_CHK=0/1 in the
-// environment restricts the check-state placement (tuning experiments).
+// Lane groups per team for the CBP-SP kernel: the smallest number of groups that fills
+// whole warps, if the CTA splits into at most 15 such teams (named barriers 1..15);
+// otherwise the whole CTA is one team.
+int team_groups_for(int Z, int groups) {
+  int a = Z, b = 32;
+  while (b) {
+    const int r = a % b;
+    a = b;
+    b = r;
+  }
+  const int tg = 32 / a;
+  if (groups % tg == 0 && groups / tg <= 15 && groups / tg >= 2) return tg;
+  return groups;
+}
+
+// Launch plan: for each layout variant the number of lane groups per CTA that gives the
+// most resident frames per SM (ties: more resident warps); the variant with the most
+// resident frames wins (ties: the earlier one in the candidate list).  CBP_PLAN_CHK=0/1
+// and CBP_PLAN_FPT=1/2 in the environment restrict the candidates (tuning experiments).
 int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan* out) {
   std::vector<Variant> cands;
   switch (alg) {
     case ALG_CBP_SP:
-      cands = {{ALG_CBP_SP, true}, {ALG_CBP_SP, false}};
+      cands = {{ALG_CBP_SP, true, 2}, {ALG_CBP_SP, false, 2}, {ALG_CBP_SP, true, 1},
+               {ALG_CBP_SP, false, 1}};
+      if (c->Z > 384) cands.push_back({ALG_CBP_SP, true, 1, true});
+      if (c->Z > 384) cands.push_back({ALG_CBP_SP, false, 1, true});
       break;
     case ALG_CBP_NMS:
+      if (c->maxdeg > kMaxDegCbpMs) return CBP_EUNSUPPORTED;
       cands = {{ALG_CBP_NMS, true}, {ALG_CBP_NMS, false}};
       break;
     case ALG_LBP_NMS:
       if (c->maxdeg > kMaxDeg) return CBP_EUNSUPPORTED;
-      cands = {{ALG_LBP_NMS, true}};
+      cands = {{ALG_LBP_NMS, false}};
       break;
     case ALG_FBP_SP:
       if (c->maxdeg > kMaxDeg) return CBP_EUNSUPPORTED;
@@ -243,10 +285,16 @@ int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan*
                   cands.end());
     }
   }
+  if (const char* e = std::getenv("CBP_PLAN_FPT")) {
+    const int want = e[0] == '2' ? 2 : 1;
+    cands.erase(std::remove_if(cands.begin(), cands.end(),
+                               [&](const Variant& v) { return v.fpt != want; }),
+                cands.end());
+  }
   const Shape sh = c->shape();
   bool found = false;
   Plan best;
-  int best_warps = -1, best_ctas = 0;
+  int best_frames = -1, best_warps = -1, best_ctas = 0;
   for (const Variant& v : cands) {
     cudaFuncAttributes fa;
     if (decoder_func_attrs(v, &fa) != cudaSuccess) return CBP_ECUDA;
@@ -260,7 +308,9 @@ int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan*
       int ctas = 0;
       if (decoder_occupancy(v, threads, smem, &ctas) != cudaSuccess) return CBP_ECUDA;
       const int warps = ctas * threads / 32;
-      if (ctas >= 1 && warps > best_warps) {
+      const int frames = ctas * F * v.fpt;
+      if (ctas >= 1 && (frames > best_frames || (frames == best_frames && warps > best_warps))) {
+        best_frames = frames;
         best_warps = warps;
         best_ctas = ctas;
         best.v = v;
@@ -273,18 +323,21 @@ int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan*
     }
   }
   if (!found) return CBP_EUNSUPPORTED;
-  // small batches: fewer frames per CTA so the frames spread over the SMs
-  const int spread = std::max(1, (batch + di.sms - 1) / di.sms);
+  // small batches: fewer lane groups per CTA so the frames spread over the SMs
+  const int per_group = best.v.fpt;
+  const int spread = std::max(1, (batch + di.sms * per_group - 1) / (di.sms * per_group));
   if (best.F > spread) {
     best.F = spread;
     best.threads = (best.F * c->Z + 31) / 32 * 32;
     best.smem = shared_fixed_bytes(best.v, sh, best.F) +
                 best.F * static_cast<size_t>(best.sh_frame) * 4;
   }
-  const long long need = (static_cast<long long>(batch) + best.F - 1) / best.F;
+  best.team_groups = team_groups_for(c->Z, best.F);
+  const long long per_cta = static_cast<long long>(best.F) * per_group;
+  const long long need = (static_cast<long long>(batch) + per_cta - 1) / per_cta;
   best.grid = static_cast<int>(std::max(1LL, std::min<long long>(need, 1LL * di.sms * best_ctas)));
-  best.ws_slot = static_cast<long long>(ws_slot_floats(best.v, sh, &best.ws_off_sv, &best.ws_off_s));
-  best.ws_bytes = static_cast<size_t>(best.grid) * best.F * best.ws_slot * sizeof(float);
+  best.ws = ws_layout(best.v, sh);
+  best.ws_bytes = static_cast<size_t>(best.grid) * best.F * best.ws.slot * sizeof(float);
   *out = best;
   return CBP_OK;
 }
@@ -508,13 +561,15 @@ int cbp_decode_ex(const cbp_code_t* c, const float* llr, uint32_t* hard_out, int
   p.stop = stop;
   p.alpha = alpha;
   p.F = pl.F;
-  p.slots = pl.grid * pl.F;
+  p.team_groups = team_groups_for(c->Z, pl.F);
+  p.slots = pl.grid * pl.F * pl.v.fpt;
   p.maxdeg = c->maxdeg;
   p.ncomp = c->ncomp;
   p.nself = c->nself;
-  p.ws_slot = pl.ws_slot;
-  p.ws_off_sv = pl.ws_off_sv;
-  p.ws_off_s = pl.ws_off_s;
+  p.ws_slot = pl.ws.slot;
+  p.ws_off_sv = pl.ws.off_sv;
+  p.ws_off_s = pl.ws.off_s;
+  p.ws_off_c = pl.ws.off_c;
   p.sh_frame = pl.sh_frame;
   cudaError_t e = launch_decoder(pl.v, p, pl.grid, pl.threads, pl.smem,
                                  reinterpret_cast<cudaStream_t>(stream));
@@ -567,7 +622,7 @@ int cbp_decode_noalloc(const cbp_code_t* c, const float* llr, uint32_t* hard_out
   // Fit the launch into the array: fewer CTAs, and if one CTA is still too big, fewer
   // frame slots per CTA.  Slots loop over frames, so any grid decodes the whole batch.
   const size_t cap = CBP_NOALLOC_SCRATCH_BYTES;
-  const size_t slot_bytes = static_cast<size_t>(pl.ws_slot) * sizeof(float);
+  const size_t slot_bytes = static_cast<size_t>(pl.ws.slot) * sizeof(float);
   if (slot_bytes > cap) return CBP_EWORKSPACE;
   if (static_cast<size_t>(pl.F) * slot_bytes > cap) {
     pl.F = static_cast<int>(cap / slot_bytes);
@@ -604,13 +659,15 @@ int cbp_decode_noalloc(const cbp_code_t* c, const float* llr, uint32_t* hard_out
   p.stop = CBP_STOP_SYNDROME;
   p.alpha = 0.75f;
   p.F = pl.F;
-  p.slots = pl.grid * pl.F;
+  p.team_groups = team_groups_for(c->Z, pl.F);
+  p.slots = pl.grid * pl.F * pl.v.fpt;
   p.maxdeg = c->maxdeg;
   p.ncomp = c->ncomp;
   p.nself = c->nself;
-  p.ws_slot = pl.ws_slot;
-  p.ws_off_sv = pl.ws_off_sv;
-  p.ws_off_s = pl.ws_off_s;
+  p.ws_slot = pl.ws.slot;
+  p.ws_off_sv = pl.ws.off_sv;
+  p.ws_off_s = pl.ws.off_s;
+  p.ws_off_c = pl.ws.off_c;
   p.sh_frame = pl.sh_frame;
   cudaError_t e = launch_decoder(pl.v, p, pl.grid, pl.threads, pl.smem,
                                  reinterpret_cast<cudaStream_t>(stream));

@@ -26,15 +26,19 @@ void phi_table_host(float* coef, float* xlo);
 
 __device__ __forceinline__ float phi_eval(float x, float xlo, const float4* __restrict__ tab) {
   x = fminf(fmaxf(x, xlo), 30.0f);
+  // below 2: nearest centre cb, t = (x - cb) * 2^-e(cb), 2^-e from the exponent field
   const uint32_t cb = (__float_as_uint(x) + 0x20000u) & 0xFFFC0000u;
-  const float u = __fmul_rn(x, 16.0f);
-  const float k = rintf(u);
-  const bool lo = x < 2.0f;
   const float tl = __fmul_rn(__fsub_rn(x, __uint_as_float(cb)),
-                             __uint_as_float((254u - (cb >> 23)) << 23));
-  const float t = lo ? tl : __fsub_rn(u, k);
+                             __uint_as_float(0x7F000000u - (cb & 0x7F800000u)));
+  // 2 to 30: k = rint(16x) by adding 1.5 * 2^23 (16x is exact and below 2^22), t = 16x - k
+  constexpr float kMagic = 12582912.0f;
+  const float y = __fmaf_rn(x, 16.0f, kMagic);
+  const float tu = __fmaf_rn(x, 16.0f, -__fsub_rn(y, kMagic));
+  const bool lo = x < 2.0f;
+  const float t = lo ? tl : tu;
   const int i = lo ? static_cast<int>(cb >> 18) - kPhiLogBase
-                   : static_cast<int>(k) + (kPhiLogCount - 32);
+                   : static_cast<int>(__float_as_uint(y) - __float_as_uint(kMagic)) +
+                         (kPhiLogCount - 32);
   const float4 c = tab[i];
   float p = __fmaf_rn(c.w, t, c.z);
   p = __fmaf_rn(p, t, c.y);
@@ -85,14 +89,16 @@ struct KParams {
   int Z, mb, nb, nnzb, N, M, E, words;
   int batch, max_iter, stop;
   float alpha;
-  int F;                 // frames per CTA
-  int slots;             // gridDim.x * F
+  int F;                 // lane groups per CTA (each decodes fpt frames)
+  int team_groups;       // lane groups per independently synchronised team (>= F: one team)
+  int slots;             // frame slots of the launch: gridDim.x * F * fpt
   int maxdeg;
   int ncomp, nself;      // columns of weight >= 2 / of weight 1
-  long long ws_slot;     // floats of workspace per frame slot
-  long long ws_off_sv;   // CBP-SP: offset (floats) of the weight-1 (Q*, phi) pairs
-  long long ws_off_s;    // CBP-SP: offset of the check-beliefs when not shared
-  int sh_frame;          // floats of shared memory per frame
+  long long ws_slot;     // floats of workspace per lane group
+  long long ws_off_sv;   // offset (floats) of the weight-1 column state
+  long long ws_off_s;    // CBP-SP: check-beliefs when not shared; min-sum: check state
+  long long ws_off_c;    // CBP min-sum: (min1, min2) per check when not shared
+  int sh_frame;          // floats of shared memory per lane group
 };
 
 enum Alg { ALG_CBP_SP = 0, ALG_CBP_NMS = 1, ALG_LBP_NMS = 2, ALG_FBP_SP = 3 };
@@ -100,28 +106,35 @@ enum Alg { ALG_CBP_SP = 0, ALG_CBP_NMS = 1, ALG_LBP_NMS = 2, ALG_FBP_SP = 3 };
 struct Variant {
   int alg;
   bool chk_shared;  // check state in shared memory (else in the workspace)
+  int fpt = 1;      // frames per lane group (CBP-SP: 1 or 2, interleaved)
+  bool wide = false;  // CBP-SP: instance that allows 1024 threads per CTA (Z > 512)
 };
 
 // Sizes that fix the shared-memory and workspace layout of a launch.
 struct Shape {
   int Z, N, M, E, nnzb, mb, nb, words, ncomp, nself;
 };
-size_t shared_fixed_bytes(const Variant& v, const Shape& s, int F);
-size_t shared_frame_floats(const Variant& v, const Shape& s);
-// workspace floats per slot; *off_sv, *off_s receive the CBP-SP offsets
-size_t ws_slot_floats(const Variant& v, const Shape& s, long long* off_sv, long long* off_s);
+size_t shared_fixed_bytes(const Variant& v, const Shape& s, int groups);
+size_t shared_frame_floats(const Variant& v, const Shape& s);  // per lane group
+// Workspace floats per lane group and the offsets of its parts (see KParams).
+struct WsLayout {
+  long long slot = 0, off_sv = 0, off_s = 0, off_c = 0;
+};
+WsLayout ws_layout(const Variant& v, const Shape& s);
 
-// Launchers (cbp_layered.cu / cbp_flood.cu).
+// Launchers (cbp_dispatch.cu).
 cudaError_t launch_decoder(const Variant& v, const KParams& p, int grid, int threads,
                            size_t smem, cudaStream_t st);
 cudaError_t decoder_func_attrs(const Variant& v, cudaFuncAttributes* a);
 cudaError_t decoder_set_smem(const Variant& v, int bytes);
 cudaError_t decoder_occupancy(const Variant& v, int threads, size_t smem, int* ctas);
-void* sp_kernel_ptr(bool chk_shared);  // cbp_sp.cu
+void* sp_kernel_ptr(bool chk_shared, int fpt, bool wide);  // cbp_sp.cu
+void* minsum_kernel_ptr(int alg, bool chk_shared);          // cbp_minsum.cu
 void* flood_kernel_ptr();              // cbp_flood.cu
 cudaError_t launch_phi(const float* x, float* y, long long n, const float4* tab, float xlo,
                        cudaStream_t st);
 
-constexpr int kMaxDeg = 32;  // row-degree limit of the two-pass (pooled) comparators
+constexpr int kMaxDeg = 32;     // row-degree limit of the two-pass (pooled) comparators
+constexpr int kMaxDegCbpMs = 64;  // CBP min-sum: one sign bit per edge in a 64-bit mask
 
 }  // namespace cbp

@@ -1,45 +1,139 @@
 // CBP, log-tanh form (Sec. IV-C, Steps 1-3): the main decoder kernel on sm_103a.
 //
-// Same frame-slot / Z-lane structure as the generic sequential kernel (one CTA holds
-// F frames of Z lanes; the Z checks of a base row run in parallel, one barrier per
-// row), with the per-frame state arranged for throughput:
-//   shared    (Q*_v, phi(|Q*_v|)) pairs of the variables whose column has weight >= 2,
-//             the check-beliefs S_c (sign bit = sgn Omega_c) when they fit, decision bits
-//   workspace C2V messages R [base entry][lane]; (Q*, phi) of weight-1 columns, which
-//             only their one check lane touches ([weight-1 column][lane]); S_c otherwise
-// A base row is processed in chunks of CH edges: the loads of a chunk (Q*, phi, S of
-// the predecessor check, R of the edge) are issued together, then the CH edge
-// updates run with independent phi evaluations, in ascending column order.
-#include "cbp_internal.cuh"
+// A CTA holds G lane groups of Z lanes; lane z of a group owns check r*Z + z of every
+// base row r for FPT frames at once (FPT = 1 or 2).  The Z checks of a base row share
+// no variable, so they run in parallel and one barrier per base row keeps the paper's
+// sequential order exactly.  The FPT frames of a group are independent: each has its
+// own sweep counter, stops on its own syndrome and is replaced by the next frame of its
+// slot at the following sweep boundary; they only share the index arithmetic and the
+// memory instructions, because their state is interleaved frame-innermost:
+//   shared    (Q*_v, phi(|Q*_v|)) per frame for the variables of weight >= 2 columns,
+//             [compact column][lane][frame]; the check-beliefs S_c (sign bit = sgn
+//             Omega_c) [check][frame] when they fit; decision bits per frame
+//   workspace C2V messages R [base entry][lane][frame]; (Q*, phi) of weight-1 columns,
+//             which only their one check lane touches, [column][lane][frame]; S_c when
+//             not shared
+// A base row is processed in chunks of CH edges: the loads of a chunk are issued
+// together, then the CH edge updates run with independent phi evaluations, in
+// ascending column order (the order of the C2B fold).
+#include "cbp_kernel_common.cuh"
 
 namespace cbp {
 namespace {
 
-struct SlotState {
-  int frame, t, unsat;
+// Vector access to FPT interleaved frames.
+template <int FPT> struct Lanes;
+template <> struct Lanes<1> {
+  __device__ static void ld_pair(const float* a, int i, float* q, float* p) {
+    const float2 v = reinterpret_cast<const float2*>(a)[i];
+    q[0] = v.x; p[0] = v.y;
+  }
+  __device__ static void st_pair(float* a, int i, const float* q, const float* p) {
+    reinterpret_cast<float2*>(a)[i] = make_float2(q[0], p[0]);
+  }
+  __device__ static void ld(const float* a, int i, float* x) { x[0] = a[i]; }
+  __device__ static void st(float* a, int i, const float* x) { a[i] = x[0]; }
+};
+template <> struct Lanes<2> {
+  __device__ static void ld_pair(const float* a, int i, float* q, float* p) {
+    const float4 v = reinterpret_cast<const float4*>(a)[i];
+    q[0] = v.x; p[0] = v.y; q[1] = v.z; p[1] = v.w;
+  }
+  __device__ static void st_pair(float* a, int i, const float* q, const float* p) {
+    reinterpret_cast<float4*>(a)[i] = make_float4(q[0], p[0], q[1], p[1]);
+  }
+  __device__ static void ld(const float* a, int i, float* x) {
+    const float2 v = reinterpret_cast<const float2*>(a)[i];
+    x[0] = v.x; x[1] = v.y;
+  }
+  __device__ static void st(float* a, int i, const float* x) {
+    reinterpret_cast<float2*>(a)[i] = make_float2(x[0], x[1]);
+  }
 };
 
-__device__ __forceinline__ int mod_add(int a, int Z) { return a >= Z ? a - Z : a; }
-__device__ __forceinline__ uint32_t sign_bit(float x) { return __float_as_uint(x) >> 31; }
+// Registers of one chunk of CH edges of a base row (FPT frames each).
+template <int FPT, int CH>
+struct Chunk {
+  float q[CH][FPT], ph[CH][FPT], sj[CH][FPT], ro[CH][FPT];
+  int qoff[CH];   // pair index of the variable in QP (weight >= 2) or SV (weight 1)
+  int roff[CH];   // predecessor R slot (base entry of c_j, lane of c_j)
+  uint32_t fl[CH];
+};
 
-// OR `bit` into the shared word `word`, one atomic per distinct word in the warp (the
-// lanes of a warp may belong to different frames, so words are matched by address).
-__device__ __forceinline__ void warp_or_bit(uint32_t* word, uint32_t bit, bool active) {
-  const unsigned act = __ballot_sync(0xffffffffu, active);
-  if (!active) return;
-  const unsigned grp = __match_any_sync(act, reinterpret_cast<unsigned long long>(word));
-  const uint32_t val = __reduce_or_sync(grp, bit);
-  if ((threadIdx.x & 31) == __ffs(grp) - 1 && val) atomicOr(word, val);
+// Loads of a chunk: (Q*, phi) of each variable, S of its predecessor check c_j, and
+// the edge's own R slot (not read in a frame's first sweep).
+template <int FPT, int CH>
+__device__ __forceinline__ void load_chunk(Chunk<FPT, CH>& c, int kb, int k1,
+                                           const BaseEdge* __restrict__ s_e, int z, int Z,
+                                           bool later, const float* QP, const float* SV,
+                                           const float* S, const float* R) {
+  using LV = Lanes<FPT>;
+#pragma unroll
+  for (int j = 0; j < CH; ++j) {
+    const int k = kb + j;
+    if (k < k1) {
+      const BaseEdge be = s_e[k];
+      const int zv = mod_add(z + be.s, Z);
+      const int idx = be.pad & 0xffff;
+      const bool self = be.flags & kSelf;
+      int zj = zv - be.ps;
+      zj = zj < 0 ? zj + Z : zj;
+      c.fl[j] = be.flags;
+      c.qoff[j] = self ? idx * Z + z : idx * Z + zv;
+      c.roff[j] = be.pe * Z + zj;
+      LV::ld_pair(self ? SV : QP, c.qoff[j], c.q[j], c.ph[j]);
+      LV::ld(S, be.pr * Z + zj, c.sj[j]);
+      if (later && !self) LV::ld(R, k * Z + z, c.ro[j]);
+    }
+  }
 }
 
-template <bool CHKS, int CH>
-__global__ void __launch_bounds__(1024, 1) cbp_sp_kernel(const KParams p) {
+// Step 2 (1) b)-e) for the edges of a chunk, in ascending column order.
+template <int FPT, int CH>
+__device__ __forceinline__ void update_chunk(const Chunk<FPT, CH>& c, int kb, int k1,
+                                             const int* t, float* Sacc, uint32_t* sig,
+                                             float xlo, const float4* __restrict__ tab,
+                                             float* QP, float* SV, float* R) {
+  using LV = Lanes<FPT>;
+#pragma unroll
+  for (int j = 0; j < CH; ++j) {
+    if (kb + j < k1) {
+      const bool self = c.fl[j] & kSelf;
+      const bool first_row = c.fl[j] & kFirst;
+      float Rn[FPT], qn[FPT], phn[FPT];
+      bool store_r = false;
+#pragma unroll
+      for (int h = 0; h < FPT; ++h) {
+        // B2V, Eqs. (s4e18), (s4e13): exclude phi(|Q*|) from S of c_j; a variable not
+        // visited before adds no C2V
+        const float mag = phi_eval(fabsf(__fsub_rn(fabsf(c.sj[j][h]), c.ph[j][h])), xlo, tab);
+        const float rb = (sign_bit(c.sj[j][h]) ^ (c.q[j][h] < 0.0f)) ? -mag : mag;
+        const bool first = (t[h] == 1) && first_row;
+        Rn[h] = first ? 0.0f : rb;
+        store_r |= !first;
+        // V2C, Eqs. (s4e20), (s4e19); weight-1 column: c_j == c_i
+        const float rold = self ? Rn[h] : (t[h] > 1 ? c.ro[j][h] : 0.0f);
+        qn[h] = __fsub_rn(__fadd_rn(c.q[j][h], Rn[h]), rold);
+        // C2B, Eq. (s4e21) as a sum of phi
+        phn[h] = phi_eval(fabsf(qn[h]), xlo, tab);
+        Sacc[h] = __fadd_rn(Sacc[h], phn[h]);
+        sig[h] ^= (qn[h] < 0.0f);
+      }
+      if (store_r && !self) LV::st(R, c.roff[j], Rn);  // R_{c_j->v} <- R^new (Eq. s4e22)
+      LV::st_pair(self ? SV : QP, c.qoff[j], qn, phn);
+    }
+  }
+}
+
+template <bool CHKS, int FPT, int CH, bool DB, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) cbp_sp_kernel(const KParams p) {
+  using LV = Lanes<FPT>;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int Z = p.Z, N = p.N, M = p.M, words = p.words, F = p.F;
+  const int Z = p.Z, N = p.N, M = p.M, words = p.words, G = p.F;
   const int tid = threadIdx.x;
-  const int f = tid / Z;
-  const int z = tid - f * Z;
-  const bool lane = f < F;
+  const int g = tid / Z;
+  const int z = tid - g * Z;
+  const bool lane = g < G;
 
   unsigned char* sp = smem;
   float4* s_tab = reinterpret_cast<float4*>(sp);
@@ -48,11 +142,11 @@ __global__ void __launch_bounds__(1024, 1) cbp_sp_kernel(const KParams p) {
   sp += sizeof(BaseEdge) * p.nnzb;
   int* s_rptr = reinterpret_cast<int*>(sp);
   sp += sizeof(int) * ((p.mb + 1 + 3) & ~3);
-  uint2* s_col = reinterpret_cast<uint2*>(sp);  // per column: (last row | shift << 16, idx | self << 16)
+  uint2* s_col = reinterpret_cast<uint2*>(sp);  // (last row | shift << 16, idx | self << 16)
   sp += sizeof(uint2) * ((p.nb + 1) & ~1);
   SlotState* s_slot = reinterpret_cast<SlotState*>(sp);
-  sp += sizeof(SlotState) * ((F + 3) & ~3);
-  float* s_frames = reinterpret_cast<float*>(sp);
+  sp += sizeof(SlotState) * ((G * FPT + 3) & ~3);
+  float* s_groups = reinterpret_cast<float*>(sp);
 
   for (int i = tid; i < kPhiSegments; i += blockDim.x) s_tab[i] = p.phi_tab[i];
   for (int i = tid; i < p.nnzb; i += blockDim.x) s_e[i] = p.edges[i];
@@ -63,188 +157,225 @@ __global__ void __launch_bounds__(1024, 1) cbp_sp_kernel(const KParams p) {
     s_col[c] = make_uint2(uint32_t(ce.r) | (uint32_t(ce.s) << 16),
                           (be.pad & 0xffffu) | ((be.flags & kSelf) ? 0x10000u : 0u));
   }
-  if (tid < F) {
-    s_slot[tid].frame = blockIdx.x * F + tid;
-    s_slot[tid].t = 0;
-    s_slot[tid].unsat = 0;
+  for (int k = tid; k < G * FPT; k += blockDim.x) {
+    s_slot[k].frame = blockIdx.x * G * FPT + k;
+    s_slot[k].t = 0;
+    s_slot[k].unsat = 0;
   }
-  // per frame, shared: QP float2 [ncomp*Z] | S [M] (CHKS) | bits [words]
-  const int ncomp = p.ncomp;
-  float* base = s_frames + static_cast<size_t>(lane ? f : 0) * p.sh_frame;
-  float2* QP = reinterpret_cast<float2*>(base);
-  float* nxt = base + 2 * static_cast<size_t>(ncomp) * Z;
-  const long long g = static_cast<long long>(blockIdx.x) * F + (lane ? f : 0);
-  float* wsl = p.ws + g * p.ws_slot;
-  float* R = wsl;
-  float2* SV = reinterpret_cast<float2*>(wsl + p.ws_off_sv);  // weight-1 columns
+  // per group, shared: QP [ncomp*Z][FPT](Q,phi) | S [M][FPT] (CHKS) | bits [FPT][wpad]
+  float* gbase = s_groups + static_cast<size_t>(lane ? g : 0) * p.sh_frame;
+  float* QP = gbase;
+  float* nxt = gbase + 2 * FPT * static_cast<size_t>(p.ncomp) * Z;
+  const long long gslot = static_cast<long long>(blockIdx.x) * G + (lane ? g : 0);
+  float* wsl = p.ws + gslot * p.ws_slot;
+  float* R = wsl;                       // [E][FPT]
+  float* SV = wsl + p.ws_off_sv;        // [nself*Z][FPT](Q,phi)
   float* S;
   if (CHKS) {
     S = nxt;
-    nxt += (M + 3) & ~3;
+    nxt += FPT * ((M + 3) & ~3);
   } else {
     S = wsl + p.ws_off_s;
   }
-  uint32_t* bits = reinterpret_cast<uint32_t*>(nxt);
+  uint32_t* bits = reinterpret_cast<uint32_t*>(nxt);   // frame h: bits + h * wpad
+  const int wpad = (words + 3) & ~3;
+  SlotState* my = s_slot + (lane ? g : 0) * FPT;
   const float4* tab = s_tab;
   const float xlo = p.phi_xlo;
+  // teams of p.team_groups lane groups (whole warps) synchronise among themselves
+  const int tg = p.team_groups;
+  const bool single_team = tg >= G;
+  const int bar_id = single_team ? 0 : 1 + (lane ? g / tg : 0);
+  const int bar_n = single_team ? static_cast<int>(blockDim.x) : tg * Z;
   __syncthreads();
 
   for (;;) {
-    const int frame = lane ? s_slot[f].frame : p.batch;
-    const bool act = frame < p.batch;
-    if (act && s_slot[f].t == 0) {  // Step 1, Eq. (s4e15): Q*_v = L_v
-      const float* src = p.llr + static_cast<long long>(frame) * N;
-      for (int c = 0; c < p.nb; ++c) {
-        const uint32_t cinfo = s_col[c].y;
-        const int idx = cinfo & 0xffff;
-        if (cinfo & 0x10000u) {
-          const int s = int(s_col[c].x >> 16);
-          SV[idx * Z + z] = make_float2(__ldg(src + c * Z + mod_add(z + s, Z)), 0.0f);
-        } else {
-          QP[idx * Z + z] = make_float2(__ldg(src + c * Z + z), 0.0f);
+    int frame[FPT], t[FPT];
+    bool act[FPT];
+    bool any = false;
+#pragma unroll
+    for (int h = 0; h < FPT; ++h) {
+      frame[h] = lane ? my[h].frame : p.batch;
+      act[h] = frame[h] < p.batch;
+      any |= act[h];
+      if (act[h] && my[h].t == 0) {  // Step 1, Eq. (s4e15): Q*_v = L_v for frame h
+        const float* src = p.llr + static_cast<long long>(frame[h]) * N;
+        for (int c = 0; c < p.nb; ++c) {
+          const uint2 ci = s_col[c];
+          const int idx = ci.y & 0xffff;
+          if (ci.y & 0x10000u) {
+            const int s = int(ci.x >> 16);
+            SV[((idx * Z + z) * FPT + h) * 2] = __ldg(src + c * Z + mod_add(z + s, Z));
+          } else {
+            QP[((idx * Z + z) * FPT + h) * 2] = __ldg(src + c * Z + z);
+          }
         }
       }
     }
-    if (!__syncthreads_or(act)) break;
-    const int t = act ? s_slot[f].t + 1 : 0;
+    if (!team_sync_or(bar_id, bar_n, any)) break;
+#pragma unroll
+    for (int h = 0; h < FPT; ++h) t[h] = act[h] ? my[h].t + 1 : 0;
+    bool later = false;  // some frame of the group is past its first sweep
+#pragma unroll
+    for (int h = 0; h < FPT; ++h) later |= t[h] > 1;
 
     for (int r = 0; r < p.mb; ++r) {
-      if (act) {
+      if (any) {
         const int k0 = s_rptr[r], k1 = s_rptr[r + 1];
-        float Sacc = 0.0f;
-        uint32_t sig = 0;
-        for (int kb = k0; kb < k1; kb += CH) {
-          float q[CH], ph[CH], sj[CH], ro[CH];
+        float Sacc[FPT];
+        uint32_t sig[FPT];
 #pragma unroll
-          for (int j = 0; j < CH; ++j) {
-            const int k = kb + j;
-            if (k < k1) {
-              const BaseEdge be = s_e[k];
-              const int zv = mod_add(z + be.s, Z);
-              const int idx = be.pad & 0xffff;
-              float2 qp;
-              if (be.flags & kSelf) qp = SV[idx * Z + z];
-              else qp = QP[idx * Z + zv];
-              q[j] = qp.x;
-              ph[j] = qp.y;
-              int zj = zv - be.ps;
-              zj = zj < 0 ? zj + Z : zj;
-              sj[j] = S[be.pr * Z + zj];
-              ro[j] = (t > 1 && !(be.flags & kSelf)) ? R[k * Z + z] : 0.0f;
-            }
+        for (int h = 0; h < FPT; ++h) {
+          Sacc[h] = 0.0f;
+          sig[h] = 0;
+        }
+        if (DB) {
+          // two register buffers: the next chunk's loads are issued before the current
+          // chunk's stores (they never alias: a row reads its own R slots, the beliefs of
+          // other rows and distinct variables, and writes predecessor R slots, its
+          // variables and its own beliefs)
+          Chunk<FPT, CH> A, B;
+          load_chunk<FPT, CH>(A, k0, k1, s_e, z, Z, later, QP, SV, S, R);
+          for (int kb = k0;;) {
+            if (kb + CH < k1) load_chunk<FPT, CH>(B, kb + CH, k1, s_e, z, Z, later, QP, SV, S, R);
+            update_chunk<FPT, CH>(A, kb, k1, t, Sacc, sig, xlo, tab, QP, SV, R);
+            kb += CH;
+            if (kb >= k1) break;
+            if (kb + CH < k1) load_chunk<FPT, CH>(A, kb + CH, k1, s_e, z, Z, later, QP, SV, S, R);
+            update_chunk<FPT, CH>(B, kb, k1, t, Sacc, sig, xlo, tab, QP, SV, R);
+            kb += CH;
+            if (kb >= k1) break;
           }
-#pragma unroll
-          for (int j = 0; j < CH; ++j) {
-            const int k = kb + j;
-            if (k < k1) {
-              const BaseEdge be = s_e[k];
-              const int zv = mod_add(z + be.s, Z);
-              const bool self = be.flags & kSelf;
-              float Rn = 0.0f;
-              if (!(t == 1 && (be.flags & kFirst))) {
-                // B2V, Eqs. (s4e18), (s4e13): exclude phi(|Q*|) from S of c_j
-                const float mag = phi_eval(fabsf(__fsub_rn(fabsf(sj[j]), ph[j])), xlo, tab);
-                Rn = (sign_bit(sj[j]) ^ (q[j] < 0.0f)) ? -mag : mag;
-                if (!self) {                   // R_{c_j->v} <- R^new (Eq. s4e22)
-                  int zj = zv - be.ps;
-                  zj = zj < 0 ? zj + Z : zj;
-                  R[be.pe * Z + zj] = Rn;
-                }
-              }
-              const float rold = self ? Rn : ro[j];
-              const float qn = __fsub_rn(__fadd_rn(q[j], Rn), rold);  // Eqs. (s4e20), (s4e19)
-              const float phn = phi_eval(fabsf(qn), xlo, tab);        // C2B, Eq. (s4e21)
-              Sacc = __fadd_rn(Sacc, phn);
-              sig ^= (qn < 0.0f);
-              const int idx = be.pad & 0xffff;
-              if (self) SV[idx * Z + z] = make_float2(qn, phn);
-              else QP[idx * Z + zv] = make_float2(qn, phn);
-            }
+        } else {
+          for (int kb = k0; kb < k1; kb += CH) {
+            Chunk<FPT, CH> A;
+            load_chunk<FPT, CH>(A, kb, k1, s_e, z, Z, later, QP, SV, S, R);
+            update_chunk<FPT, CH>(A, kb, k1, t, Sacc, sig, xlo, tab, QP, SV, R);
           }
         }
-        S[r * Z + z] = sig ? -Sacc : Sacc;     // Eq. (s4e23)
+        float sv[FPT];
+#pragma unroll
+        for (int h = 0; h < FPT; ++h) sv[h] = sig[h] ? -Sacc[h] : Sacc[h];
+        LV::st(S, r * Z + z, sv);  // Eq. (s4e23); the sign bit carries sgn(Omega)
       }
-      __syncthreads();
+      team_sync(bar_id, bar_n);
     }
 
     // ---- flushed posterior, hard decisions (Eq. s2e7)
-    if (act)
-      for (int w = z; w < words; w += Z) bits[w] = 0u;
-    if (tid < F) s_slot[tid].unsat = 0;
-    __syncthreads();
-    {
-      float* so = (act && p.soft) ? p.soft + static_cast<long long>(frame) * N : nullptr;
-      for (int c = 0; c < p.nb; ++c) {
-        const uint2 ci = s_col[c];
-        const int idx = ci.y & 0xffff;
-        const int sk = int(ci.x >> 16), rk = int(ci.x & 0xffff);
-        int v = 0;
-        bool neg = false;
-        if (act) {
-          float2 qp;
-          float Sk;
-          if (ci.y & 0x10000u) {  // weight-1 column: lane z owns its single check (rk, z)
-            qp = SV[idx * Z + z];
-            Sk = S[rk * Z + z];
-            v = c * Z + mod_add(z + sk, Z);
-          } else {
-            qp = QP[idx * Z + z];
-            int zk = z - sk;
-            zk = zk < 0 ? zk + Z : zk;
-            Sk = S[rk * Z + zk];
-            v = c * Z + z;
-          }
-          const float mag = phi_eval(fabsf(__fsub_rn(fabsf(Sk), qp.y)), xlo, tab);
-          const float lb = __fadd_rn(qp.x, (sign_bit(Sk) ^ (qp.x < 0.0f)) ? -mag : mag);
-          neg = lb < 0.0f;
-          if (so) so[v] = lb;
+#pragma unroll
+    for (int h = 0; h < FPT; ++h)
+      if (act[h])
+        for (int w = z; w < words; w += Z) bits[h * wpad + w] = 0u;
+    if (lane && z == 0)
+#pragma unroll
+      for (int h = 0; h < FPT; ++h) my[h].unsat = 0;
+    team_sync(bar_id, bar_n);
+    for (int c = 0; c < p.nb; ++c) {
+      const uint2 ci = s_col[c];
+      const int idx = ci.y & 0xffff;
+      const int sk = int(ci.x >> 16), rk = int(ci.x & 0xffff);
+      float qv[FPT], pv[FPT], Sk[FPT];
+      int v = 0;
+      if (any) {
+        if (ci.y & 0x10000u) {  // weight-1 column: lane z owns its single check (rk, z)
+          LV::ld_pair(SV, idx * Z + z, qv, pv);
+          LV::ld(S, rk * Z + z, Sk);
+          v = c * Z + mod_add(z + sk, Z);
+        } else {
+          LV::ld_pair(QP, idx * Z + z, qv, pv);
+          int zk = z - sk;
+          zk = zk < 0 ? zk + Z : zk;
+          LV::ld(S, rk * Z + zk, Sk);
+          v = c * Z + z;
         }
-        warp_or_bit(bits + (v >> 5), neg ? (1u << (v & 31)) : 0u, act);
+      }
+#pragma unroll
+      for (int h = 0; h < FPT; ++h) {
+        bool neg = false;
+        if (act[h]) {
+          const float mag = phi_eval(fabsf(__fsub_rn(fabsf(Sk[h]), pv[h])), xlo, tab);
+          const float lb = __fadd_rn(qv[h], (sign_bit(Sk[h]) ^ (qv[h] < 0.0f)) ? -mag : mag);
+          neg = lb < 0.0f;
+          if (p.soft) p.soft[static_cast<long long>(frame[h]) * N + v] = lb;
+        }
+        warp_or_bit(bits + h * wpad + (v >> 5), neg ? (1u << (v & 31)) : 0u, act[h]);
       }
     }
-    __syncthreads();
-    // ---- syndrome; a frame stops scanning at its first unsatisfied check row
-    if (act) {
-      for (int r = 0; r < p.mb; ++r) {
-        uint32_t pr = 0;
+    team_sync(bar_id, bar_n);
+    // ---- syndrome; a frame stops scanning once one of its checks is unsatisfied
+    if (any) {
+      bool open[FPT];
+      bool scan = false;
+#pragma unroll
+      for (int h = 0; h < FPT; ++h) {
+        open[h] = act[h];
+        scan |= open[h];
+      }
+      for (int r = 0; r < p.mb && scan; ++r) {
+        uint32_t pr[FPT];
+#pragma unroll
+        for (int h = 0; h < FPT; ++h) pr[h] = 0;
         for (int k = s_rptr[r]; k < s_rptr[r + 1]; ++k) {
           const BaseEdge be = s_e[k];
           const int v = be.c * Z + mod_add(z + be.s, Z);
-          pr ^= bits[v >> 5] >> (v & 31);
+#pragma unroll
+          for (int h = 0; h < FPT; ++h) pr[h] ^= bits[h * wpad + (v >> 5)] >> (v & 31);
         }
-        if (pr & 1u) s_slot[f].unsat = 1;
-        if (*static_cast<volatile int*>(&s_slot[f].unsat)) break;
+        scan = false;
+#pragma unroll
+        for (int h = 0; h < FPT; ++h) {
+          if (open[h] && (pr[h] & 1u)) my[h].unsat = 1;
+          open[h] = open[h] && !*static_cast<volatile int*>(&my[h].unsat);
+          scan |= open[h];
+        }
       }
     }
-    __syncthreads();
-    bool done = false;
-    if (act) {
-      const bool ok = s_slot[f].unsat == 0;
-      done = (ok && p.stop == CBP_STOP_SYNDROME) || t >= p.max_iter;
-      if (done) {
-        uint32_t* ho = p.hard + static_cast<long long>(frame) * words;
-        for (int w = z; w < words; w += Z) ho[w] = bits[w];
-        if (z == 0) p.iters[frame] = ok ? t : -t;
+    team_sync(bar_id, bar_n);
+    bool done[FPT];
+#pragma unroll
+    for (int h = 0; h < FPT; ++h) {
+      done[h] = false;
+      if (act[h]) {
+        const bool ok = my[h].unsat == 0;
+        done[h] = (ok && p.stop == CBP_STOP_SYNDROME) || t[h] >= p.max_iter;
+        if (done[h]) {
+          uint32_t* ho = p.hard + static_cast<long long>(frame[h]) * words;
+          for (int w = z; w < words; w += Z) ho[w] = bits[h * wpad + w];
+          if (z == 0) p.iters[frame[h]] = ok ? t[h] : -t[h];
+        }
       }
     }
-    __syncthreads();
-    if (act && z == 0) {
-      if (done) {
-        s_slot[f].frame = frame + p.slots;
-        s_slot[f].t = 0;
-      } else {
-        s_slot[f].t = t;
-      }
+    team_sync(bar_id, bar_n);
+    if (z == 0) {
+#pragma unroll
+      for (int h = 0; h < FPT; ++h)
+        if (act[h]) {
+          if (done[h]) {
+            my[h].frame = frame[h] + p.slots;
+            my[h].t = 0;
+          } else {
+            my[h].t = t[h];
+          }
+        }
     }
-    __syncthreads();
+    team_sync(bar_id, bar_n);
   }
 }
 
 }  // namespace
 
-void* sp_kernel_ptr(bool chk_shared) {
-  return chk_shared ? reinterpret_cast<void*>(&cbp_sp_kernel<true, 4>)
-                    : reinterpret_cast<void*>(&cbp_sp_kernel<false, 4>);
+void* sp_kernel_ptr(bool chk_shared, int fpt, bool wide) {
+  // wide: up to 1024 threads per CTA (Z > 512), fewer registers per thread
+  if (wide)
+    return chk_shared ? reinterpret_cast<void*>(&cbp_sp_kernel<true, 1, 2, true, 1024>)
+                      : reinterpret_cast<void*>(&cbp_sp_kernel<false, 1, 2, true, 1024>);
+  if (fpt == 2)
+    return chk_shared ? reinterpret_cast<void*>(&cbp_sp_kernel<true, 2, 4, true, 384>)
+                      : reinterpret_cast<void*>(&cbp_sp_kernel<false, 2, 4, true, 384>);
+  // one frame per lane group, up to 768 threads: two 384-lane teams per CTA progress
+  // independently and hide each other's memory latency
+  return chk_shared ? reinterpret_cast<void*>(&cbp_sp_kernel<true, 1, 4, false, 768>)
+                    : reinterpret_cast<void*>(&cbp_sp_kernel<false, 1, 4, false, 768>);
 }
 
 }  // namespace cbp
