@@ -32,13 +32,13 @@ EBN0_OPERATING = 2.5
 FRAMES = 65536
 MAX_ITER = 20
 
-# Algorithmic lane operations per unit (derived in the design doc):
-#   phi evaluation 14; CBP-SP edge update 40 (B2V 16, V2C 2, C2B 16, indexing 6);
-#   flush per variable 18; syndrome per edge 3.
-OPS_PHI = 14
-OPS_EDGE = {"cbp_sp": 40, "cbp_nms": 16, "lbp_nms": 14, "fbp_sp": 44}
-OPS_VAR = {"cbp_sp": 18, "cbp_nms": 8, "lbp_nms": 2, "fbp_sp": 3}
-OPS_SYN = 3
+# Algorithmic issue slots per unit: the minimal instruction mix (FP32/INT32 arithmetic
+# and the memory instructions) of one edge update of one sweep, of the syndrome work
+# per edge and of the end-of-sweep posterior per variable, for each algorithm as
+# defined (phi evaluation: 21).  Derivation in the design doc.
+OPS_EDGE = {"cbp_sp": 64, "cbp_nms": 31, "lbp_nms": 28, "fbp_sp": 64}
+OPS_VAR = {"cbp_sp": 30, "cbp_nms": 10, "lbp_nms": 3, "fbp_sp": 5}
+OPS_SYN = 4
 
 
 def load_peaks():
@@ -253,7 +253,7 @@ def run_ours(args, rank, world, dist):
     peak_ops = sms * 128 * sm_mhz * 1e6 / 1e12  # T lane-ops/s at the sampled SM clock
     ops = alu_ops(args.alg, qc, st["sweeps_total"])
     achieved = ops / (ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "T issue-slots/s",
                 "frac": achieved / peak_ops, "traffic": args.traffic,
                 "peak_source": f"{sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (sampled SM clock)",
                 "units": {"edge_sweeps": qc.E * st["sweeps_total"],
@@ -275,8 +275,11 @@ def run_ours(args, rank, world, dist):
             torch.cuda.synchronize()
             cms = timed_steps(torch, f, 2, stream)
             cs = frame_stats(torch, cbp, qc, hard, iters, cw)
+            c_ops = alu_ops(alg, qc, cs["sweeps_total"]) / (cms / 1e3) / 1e12
             comparators[alg] = {"gbps": K * B / (cms / 1e3) / 1e9, "ms_per_step": cms,
-                                "fer": cs["fer"], "ber": cs["ber"], "mean_iters": cs["mean_iters"]}
+                                "fer": cs["fer"], "ber": cs["ber"], "mean_iters": cs["mean_iters"],
+                                "alu_frac": c_ops / peak_ops,
+                                "launch": code.launch_info(B, alg)}
         ws = code.workspace(B, args.alg)
 
     e2e = None
@@ -323,6 +326,7 @@ def run_ours(args, rank, world, dist):
             "coded_gbps": world * qc.N * B / (ms / 1e3) / 1e9,
             "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps,
             "roofline": roofline, "cpu_baseline": cpu, "comparators": comparators,
+            "launch": code.launch_info(B, args.alg),
         }
         print(json.dumps(line), flush=True)
 

@@ -121,6 +121,14 @@ int cbp_decode_ex(const cbp_code_t* code, const float* llr, uint32_t* hard_out,
                   int32_t* iters_out, int max_iter, int batch, void* workspace,
                   size_t workspace_bytes, cbp_stream_t stream, const cbp_opts_t* opts);
 
+/* The launch a decode of `batch` frames with `opts` would use (for tuning and reports):
+ *   info[0] resident frames per SM      info[1] threads per CTA
+ *   info[2] CTAs per SM                 info[3] lane groups per CTA
+ *   info[4] frames per lane group       info[5] 1 if the check state is in shared memory
+ *   info[6] CTAs launched               info[7] lane groups per synchronising team
+ * `info` is a host array of 8 ints.  Nothing is launched. */
+int cbp_launch_info(const cbp_code_t* code, int batch, const cbp_opts_t* opts, int* info);
+
 /* Size of the decoder scratch array compiled into the library for cbp_decode_noalloc. */
 #define CBP_NOALLOC_SCRATCH_BYTES (16u << 20)
 

@@ -24,7 +24,8 @@ STATUS = {0: "CBP_OK", -1: "CBP_EINVAL", -2: "CBP_ENOMEM", -3: "CBP_ECUDA",
 
 # Every symbol include/cbp.h declares (checked by the ABI test).
 EXPORTS = ("cbp_code_create", "cbp_code_destroy", "cbp_code_info", "cbp_workspace_bytes",
-           "cbp_decode", "cbp_decode_ex", "cbp_decode_noalloc", "cbp_phi", "cbp_strerror")
+           "cbp_launch_info", "cbp_decode", "cbp_decode_ex", "cbp_decode_noalloc", "cbp_phi",
+           "cbp_strerror")
 
 
 class CbpError(RuntimeError):
@@ -59,6 +60,8 @@ def lib(build_if_needed: bool = True):
             L.cbp_code_info.argtypes = [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]
             L.cbp_workspace_bytes.restype = I
             L.cbp_workspace_bytes.argtypes = [P, I, C.POINTER(_Opts), C.POINTER(Z)]
+            L.cbp_launch_info.restype = I
+            L.cbp_launch_info.argtypes = [P, I, C.POINTER(_Opts), C.POINTER(I)]
             L.cbp_decode.restype = I
             L.cbp_decode.argtypes = [P, P, P, P, I, I, P, Z, P]
             L.cbp_decode_ex.restype = I
@@ -132,6 +135,15 @@ class Code:
         if self._ws is None or self._ws.numel() < need:
             self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=f"cuda:{self.device}")
         return self._ws
+
+    def launch_info(self, batch: int, alg: str = "cbp_sp") -> dict:
+        """The launch plan cbp_decode_ex would use (cbp_launch_info)."""
+        info = (C.c_int * 8)()
+        o = _opts(alg, 0.75, "syndrome", None)
+        _check("cbp_launch_info", lib().cbp_launch_info(self._h, int(batch), C.byref(o), info))
+        keys = ("frames_per_sm", "threads_per_cta", "ctas_per_sm", "lane_groups_per_cta",
+                "frames_per_lane_group", "check_state_shared", "ctas", "team_lane_groups")
+        return dict(zip(keys, list(info)))
 
     # ------------------------------------------------------------------ decode
     def decode_into(self, llr: torch.Tensor, hard: torch.Tensor, iters: torch.Tensor,

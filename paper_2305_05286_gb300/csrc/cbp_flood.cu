@@ -17,7 +17,37 @@ struct SlotState {
 
 __device__ __forceinline__ int mod_add(int a, int Z) { return a >= Z ? a - Z : a; }
 
-__global__ void __launch_bounds__(1024, 1) flood_kernel(const KParams p) {
+// Eqs. (s3e1), (s3e2) for check (r, z): d <= D edges starting at base entry k0.
+template <int D>
+__device__ __forceinline__ void fbp_check(const BaseEdge* __restrict__ s_e, int k0, int d, int z,
+                                          int Z, int t, const float* lam, float* R, float xlo,
+                                          const float4* __restrict__ tab) {
+  float ph[D];
+  uint32_t neg = 0, sig = 0;
+  float S = 0.0f;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    if (j < d) {
+      const BaseEdge be = s_e[k0 + j];
+      const int v = be.c * Z + mod_add(z + be.s, Z);
+      const float q = __fsub_rn(lam[v], t > 1 ? R[(k0 + j) * Z + z] : 0.0f);
+      const uint32_t n = q < 0.0f;
+      neg |= n << j;
+      sig ^= n;
+      ph[j] = phi_eval(fabsf(q), xlo, tab);
+      S = __fadd_rn(S, ph[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    if (j < d) {
+      const float mag = phi_eval(fabsf(__fsub_rn(S, ph[j])), xlo, tab);
+      R[(k0 + j) * Z + z] = (sig ^ ((neg >> j) & 1u)) ? -mag : mag;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(768, 1) flood_kernel(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int Z = p.Z, N = p.N, words = p.words, F = p.F;
   const int tid = threadIdx.x;
@@ -74,29 +104,9 @@ __global__ void __launch_bounds__(1024, 1) flood_kernel(const KParams p) {
       for (int w = z; w < words; w += Z) bits[w] = 0u;
       for (int r = 0; r < p.mb; ++r) {
         const int k0 = s_rptr[r], d = s_rptr[r + 1] - k0;
-        float ph[kMaxDeg];
-        uint32_t neg = 0, sig = 0;
-        float S = 0.0f;
-#pragma unroll
-        for (int j = 0; j < kMaxDeg; ++j) {
-          if (j < d) {
-            const BaseEdge be = s_e[k0 + j];
-            const int v = be.c * Z + mod_add(z + be.s, Z);
-            const float q = __fsub_rn(lam[v], t > 1 ? R[(k0 + j) * Z + z] : 0.0f);
-            const uint32_t n = q < 0.0f;
-            neg |= n << j;
-            sig ^= n;
-            ph[j] = phi_eval(fabsf(q), xlo, s_tab);
-            S = __fadd_rn(S, ph[j]);
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < kMaxDeg; ++j) {
-          if (j < d) {
-            const float mag = phi_eval(fabsf(__fsub_rn(S, ph[j])), xlo, s_tab);
-            R[(k0 + j) * Z + z] = (sig ^ ((neg >> j) & 1u)) ? -mag : mag;
-          }
-        }
+        if (d <= 8) fbp_check<8>(s_e, k0, d, z, Z, t, lam, R, xlo, s_tab);
+        else if (d <= 16) fbp_check<16>(s_e, k0, d, z, Z, t, lam, R, xlo, s_tab);
+        else fbp_check<kMaxDeg>(s_e, k0, d, z, Z, t, lam, R, xlo, s_tab);
       }
     }
     if (tid < F) s_slot[tid].unsat = 0;

@@ -226,7 +226,7 @@ int gf2_rank(const int32_t* base, int mb, int nb, int Z) {
 
 struct Plan {
   Variant v{};  // F below counts lane groups; a group decodes v.fpt frames
-  int F = 0, threads = 0, grid = 0;
+  int F = 0, threads = 0, grid = 0, ctas_per_sm = 0, frames_per_sm = 0;
   int team_groups = 0;  // lane groups per team (CBP-SP); >= F means one team
   size_t smem = 0;
   WsLayout ws{};
@@ -333,6 +333,8 @@ int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan*
                 best.F * static_cast<size_t>(best.sh_frame) * 4;
   }
   best.team_groups = team_groups_for(c->Z, best.F);
+  best.ctas_per_sm = best_ctas;
+  best.frames_per_sm = best_frames;
   const long long per_cta = static_cast<long long>(best.F) * per_group;
   const long long need = (static_cast<long long>(batch) + per_cta - 1) / per_cta;
   best.grid = static_cast<int>(std::max(1LL, std::min<long long>(need, 1LL * di.sms * best_ctas)));
@@ -512,6 +514,29 @@ int cbp_workspace_bytes(const cbp_code_t* c, int batch, const cbp_opts_t* opts, 
   Plan pl;
   if (int rc = make_plan(c, *di, alg, batch, &pl)) return rc;
   *bytes = pl.ws_bytes;
+  return CBP_OK;
+}
+
+int cbp_launch_info(const cbp_code_t* c, int batch, const cbp_opts_t* opts, int* info) {
+  if (!c || !info || batch < 1) return CBP_EINVAL;
+  int alg, stop;
+  float alpha;
+  float* soft;
+  if (int rc = check_opts(opts, &alg, &alpha, &stop, &soft)) return rc;
+  DeviceInfo* di = nullptr;
+  int dev = 0;
+  if (int rc = current_device(&di, &dev)) return rc;
+  if (dev != c->dev) return CBP_EDEVICE;
+  Plan pl;
+  if (int rc = make_plan(c, *di, alg, batch, &pl)) return rc;
+  info[0] = pl.frames_per_sm;
+  info[1] = pl.threads;
+  info[2] = pl.ctas_per_sm;
+  info[3] = pl.F;
+  info[4] = pl.v.fpt;
+  info[5] = pl.v.chk_shared ? 1 : 0;
+  info[6] = pl.grid;
+  info[7] = pl.team_groups;
   return CBP_OK;
 }
 

@@ -26,6 +26,68 @@ namespace {
 
 constexpr float kInf = __builtin_huge_valf();
 
+// Layered NMS on one check (lane z, check m = r*Z + z, d <= D edges): pass 1 forms
+// Q = Lambda - R_old (Eq. s2e10) and the minima, pass 2 forms R_new and
+// Lambda = Q + R_new (Eq. s2e12).  The V2C messages of the row stay in registers.
+template <int D>
+__device__ __forceinline__ void lbp_row(const BaseEdge* __restrict__ s_e, int k0, int d, int m,
+                                        int z, int Z, int t, float alpha, float* VAR, float* SV,
+                                        uint4* AUX) {
+  float r1 = 0.0f, r2 = 0.0f;
+  uint32_t osig = 0, oidx = 0, osg = 0;
+  if (t > 1) {  // rebuild R_old from the check's state of the previous sweep
+    const uint4 a = AUX[m];
+    r1 = __fmul_rn(alpha, fabsf(__uint_as_float(a.x)));
+    r2 = __fmul_rn(alpha, __uint_as_float(a.y));
+    osig = a.x >> 31;
+    oidx = a.z;
+    osg = a.w;
+  }
+  float qv[D];
+  float m1 = kInf, m2 = kInf;
+  uint32_t idx = 0, sig = 0, sg = 0;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    if (j < d) {
+      const BaseEdge be = s_e[k0 + j];
+      const int cidx = be.pad & 0xffff;
+      const float lam = (be.flags & kSelf) ? SV[cidx * Z + z]
+                                           : VAR[cidx * Z + mod_add(z + be.s, Z)];
+      float rold = 0.0f;
+      if (t > 1) {
+        const float rm = (static_cast<uint32_t>(j) == oidx) ? r2 : r1;
+        rold = (osig ^ ((osg >> j) & 1u)) ? -rm : rm;
+      }
+      const float q = __fsub_rn(lam, rold);
+      qv[j] = q;
+      const float a = fabsf(q);
+      if (a < m1) {
+        m2 = m1;
+        m1 = a;
+        idx = j;
+      } else if (a < m2) {
+        m2 = a;
+      }
+      const uint32_t neg = q < 0.0f;
+      sig ^= neg;
+      sg |= neg << j;
+    }
+  }
+  const float n1 = __fmul_rn(alpha, m1), n2 = __fmul_rn(alpha, m2);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    if (j < d) {
+      const BaseEdge be = s_e[k0 + j];
+      const int cidx = be.pad & 0xffff;
+      const float rm = (static_cast<uint32_t>(j) == idx) ? n2 : n1;
+      const float lam = __fadd_rn(qv[j], (sig ^ ((sg >> j) & 1u)) ? -rm : rm);
+      if (be.flags & kSelf) SV[cidx * Z + z] = lam;
+      else VAR[cidx * Z + mod_add(z + be.s, Z)] = lam;
+    }
+  }
+  AUX[m] = make_uint4(__float_as_uint(sig ? -m1 : m1), __float_as_uint(m2), idx, sg);
+}
+
 template <int ALG, bool CHKS, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
   constexpr bool CBP = (ALG == ALG_CBP_NMS);
@@ -180,61 +242,10 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
           CHK[m] = make_float2(sig ? -m1 : m1, m2);
           AUX[m] = make_uint4(idx, static_cast<uint32_t>(sg), static_cast<uint32_t>(sg >> 32), 0u);
         } else {
-          // layered NMS: pass 1 forms Q = Lambda - R_old (Eq. s2e10) and the minima,
-          // pass 2 forms R_new and Lambda = Q + R_new (Eq. s2e12)
-          float r1 = 0.0f, r2 = 0.0f;
-          uint32_t osig = 0, oidx = 0, osg = 0;
-          if (t > 1) {
-            const uint4 a = AUX[m];
-            r1 = __fmul_rn(alpha, fabsf(__uint_as_float(a.x)));
-            r2 = __fmul_rn(alpha, __uint_as_float(a.y));
-            osig = a.x >> 31;
-            oidx = a.z;
-            osg = a.w;
-          }
-          float qv[kMaxDeg];
-          float m1 = kInf, m2 = kInf;
-          uint32_t idx = 0, sig = 0, sg = 0;
-#pragma unroll
-          for (int j = 0; j < kMaxDeg; ++j) {
-            if (j < d) {
-              const BaseEdge be = s_e[k0 + j];
-              const int cidx = be.pad & 0xffff;
-              const float lam = (be.flags & kSelf) ? SV[cidx * Z + z]
-                                                   : VAR[cidx * Z + mod_add(z + be.s, Z)];
-              float rold = 0.0f;
-              if (t > 1) {
-                const float rm = (static_cast<uint32_t>(j) == oidx) ? r2 : r1;
-                rold = (osig ^ ((osg >> j) & 1u)) ? -rm : rm;
-              }
-              const float q = __fsub_rn(lam, rold);
-              qv[j] = q;
-              const float a = fabsf(q);
-              if (a < m1) {
-                m2 = m1;
-                m1 = a;
-                idx = j;
-              } else if (a < m2) {
-                m2 = a;
-              }
-              const uint32_t neg = q < 0.0f;
-              sig ^= neg;
-              sg |= neg << j;
-            }
-          }
-          const float n1 = __fmul_rn(alpha, m1), n2 = __fmul_rn(alpha, m2);
-#pragma unroll
-          for (int j = 0; j < kMaxDeg; ++j) {
-            if (j < d) {
-              const BaseEdge be = s_e[k0 + j];
-              const int cidx = be.pad & 0xffff;
-              const float rm = (static_cast<uint32_t>(j) == idx) ? n2 : n1;
-              const float lam = __fadd_rn(qv[j], (sig ^ ((sg >> j) & 1u)) ? -rm : rm);
-              if (be.flags & kSelf) SV[cidx * Z + z] = lam;
-              else VAR[cidx * Z + mod_add(z + be.s, Z)] = lam;
-            }
-          }
-          AUX[m] = make_uint4(__float_as_uint(sig ? -m1 : m1), __float_as_uint(m2), idx, sg);
+          // layered NMS, unrolled for the smallest degree bucket that holds the row
+          if (d <= 8) lbp_row<8>(s_e, k0, d, m, z, Z, t, alpha, VAR, SV, AUX);
+          else if (d <= 16) lbp_row<16>(s_e, k0, d, m, z, Z, t, alpha, VAR, SV, AUX);
+          else lbp_row<kMaxDeg>(s_e, k0, d, m, z, Z, t, alpha, VAR, SV, AUX);
         }
       }
       team_sync(bar_id, bar_n);
