@@ -129,6 +129,39 @@ int cbp_decode_ex(const cbp_code_t* code, const float* llr, uint32_t* hard_out,
  * `info` is a host array of 8 ints.  Nothing is launched. */
 int cbp_launch_info(const cbp_code_t* code, int batch, const cbp_opts_t* opts, int* info);
 
+/* ---- Weighted CBP: the differentiable decoder --------------------------------------
+ * The B2V message of Eq. (s4e18) from check c_j is scaled by weights[tau * mb + b], where
+ * tau in [0, T) is the sweep (0-based) in which c_j formed its belief and b is c_j's base
+ * row: R^new = sgn * (w * phi(|S_cj - phi(|Q*_v|)|)).  The decoder runs exactly T sweeps
+ * (no stop) and outputs the flushed posterior after the last sweep (tau = T - 1).  With
+ * every weight 1 the output equals cbp_decode_ex(CBP_ALG_CBP_SP, CBP_STOP_NONE, T sweeps).
+ * The paper has no weights; they follow the usual unrolled-decoder construction.
+ *
+ * Bytes of device workspace cbp_decode_weighted / cbp_decode_grad need for `batch` frames,
+ * T sweeps and a state checkpoint every `ckpt_every` sweeps. */
+int cbp_grad_workspace_bytes(const cbp_code_t* code, int batch, int T, int ckpt_every,
+                             size_t* bytes);
+
+/* Forward: soft_out [batch][N] fp32 (device) = the weighted decoder's posterior LLRs.
+ *   weights  device fp32 [T][mb];  T >= 1, 1 <= ckpt_every <= T;  Z <= 512
+ *   workspace receives the checkpoints cbp_decode_grad needs: keep it unchanged between
+ *   the two calls.  Asynchronous on `stream`; allocates nothing. */
+int cbp_decode_weighted(const cbp_code_t* code, const float* llr, const float* weights, int T,
+                        int ckpt_every, int batch, float* soft_out, void* workspace,
+                        size_t workspace_bytes, cbp_stream_t stream);
+
+/* Backward of cbp_decode_weighted (same code, llr, weights, T, ckpt_every, batch and the
+ * workspace that forward call left): from grad_soft = dLoss/dsoft_out [batch][N], writes
+ * grad_weights [T][mb] (summed over the frames) and, if not NULL, grad_llr [batch][N].
+ * Reverse-mode through the sweeps in reverse order, each checkpoint segment recomputed;
+ * phi is differentiated as the evaluated cubic, |x| and the clamps with derivative 0 at
+ * their kinks, signs as constants.  Summation order of the gradients is not fixed
+ * (atomic adds). */
+int cbp_decode_grad(const cbp_code_t* code, const float* llr, const float* weights, int T,
+                    int ckpt_every, int batch, const float* grad_soft, float* grad_weights,
+                    float* grad_llr, void* workspace, size_t workspace_bytes,
+                    cbp_stream_t stream);
+
 /* Size of the decoder scratch array compiled into the library for cbp_decode_noalloc. */
 #define CBP_NOALLOC_SCRATCH_BYTES (16u << 20)
 

@@ -16,6 +16,8 @@
 //   CBP normalized min-sum: Eqs. (s4e18xx), (s4e21xx), Sec. IV-D.
 //   Layered BP (LBP): Eqs. (s2e10), (s2e12) with the shared-value check update (s3e2).
 //   Flooding BP (FBP): Eqs. (s2e3)/(s3e1), (s2e4)/(s3e2), (s2e6), (s2e7).
+//   Weighted CBP (learnable scale per sweep x base row on the B2V message) and its
+//   reverse-mode adjoint in FP64, for the differentiable decoder.
 //
 // Readings of the paper (where it is silent or garbled):
 //   * Eq. (s4e22) stores R_{c_i->v} <- R^new_{c_j->v}; read as R_{c_j->v} <- R^new_{c_j->v}
@@ -145,7 +147,7 @@ inline double phi_t(double x) { return phi64(x); }
 // Tanner graph of a QC code:  H[r*Z+i, c*Z+(i+s)%Z] = 1
 // ---------------------------------------------------------------------------
 struct Graph {
-  int N = 0, M = 0, E = 0;
+  int N = 0, M = 0, E = 0, Z = 1, mb = 0;
   std::vector<int> cptr, cvar, echk;  // check -> edges (ascending variable); edge -> check
   std::vector<int> vptr, vedge;       // variable -> edges (ascending check)
 };
@@ -473,6 +475,143 @@ struct Frame {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Weighted CBP (a learnable scale per sweep x base row on the B2V message) and its
+// reverse-mode adjoint.  Reading: the C2V message R^new_{c_j->v} of Eq. (s4e18) is
+// multiplied by w[tau][b] where tau is the sweep in which Omega_{c_j} was formed and b
+// the base row of c_j; the flushed posterior after the last sweep uses tau = T.
+// T sweeps, no early stop.  w = 1 gives CBP (log-tanh form).  Rn = sgn * (w * mag).
+// ---------------------------------------------------------------------------
+template <class T>
+struct WStep {             // one edge update of the forward, for the reverse pass
+  int v, e, ej, cj, ci, widx;  // ej = -1: first visit (no B2V)
+  T d, mag, sgn, w, qn, phn;
+};
+
+template <class T>
+inline T dphi_t(T x);  // derivative of phi (0 outside the clamp range)
+template <>
+inline double dphi_t<double>(double x) {
+  if (!(x > xlo64()) || x > kXhi64) return 0.0;
+  return -1.0 / std::sinh(x);
+}
+
+template <class T>
+void weighted_forward(const Graph& g, const T* L, const T* w, int Tsw, T* soft,
+                      std::vector<WStep<T>>* tape, std::vector<T>* lb_parts) {
+  const int N = g.N, M = g.M, E = g.E;
+  std::vector<T> Q(L, L + N), Ph(N, T(0)), S(M, T(0)), R(E, T(0));
+  std::vector<uint8_t> sg(M, 0);
+  std::vector<int> last(N, -1), formed(M, 0);
+  for (int t = 1; t <= Tsw; ++t)
+    for (int m = 0; m < M; ++m) {
+      T Sacc = T(0);
+      int sig = 0;
+      for (int e = g.cptr[m]; e < g.cptr[m + 1]; ++e) {
+        const int v = g.cvar[e];
+        WStep<T> st{};
+        st.v = v;
+        st.e = e;
+        st.ci = m;
+        st.ej = last[v];
+        T Rn = T(0);
+        if (last[v] >= 0) {
+          const int cj = g.echk[last[v]];
+          st.cj = cj;
+          st.d = S[cj] - Ph[v];
+          st.mag = phi_t(std::fabs(st.d));
+          st.sgn = (sg[cj] ^ (Q[v] < T(0))) ? T(-1) : T(1);
+          st.widx = (formed[cj] - 1) * g.mb + cj / g.Z;
+          st.w = w[st.widx];
+          Rn = st.sgn * (st.w * st.mag);
+          R[last[v]] = Rn;
+        }
+        const T lam = Q[v] + Rn;
+        const T qn = lam - R[e];
+        const T ph = phi_t(std::fabs(qn));
+        Sacc = Sacc + ph;
+        sig ^= (qn < T(0));
+        st.qn = qn;
+        st.phn = ph;
+        Q[v] = qn;
+        Ph[v] = ph;
+        last[v] = e;
+        if (tape) tape->push_back(st);
+      }
+      S[m] = Sacc;
+      sg[m] = static_cast<uint8_t>(sig);
+      formed[m] = t;
+    }
+  // flushed posterior with tau = T
+  if (lb_parts) lb_parts->assign(4 * static_cast<size_t>(N), T(0));
+  for (int v = 0; v < N; ++v) {
+    const int cj = g.echk[last[v]];
+    const T d = S[cj] - Ph[v];
+    const T mag = phi_t(std::fabs(d));
+    const T sgn = (sg[cj] ^ (Q[v] < T(0))) ? T(-1) : T(1);
+    const int widx = (Tsw - 1) * g.mb + cj / g.Z;
+    soft[v] = Q[v] + sgn * (w[widx] * mag);
+    if (lb_parts) {
+      (*lb_parts)[4 * v + 0] = d;
+      (*lb_parts)[4 * v + 1] = mag;
+      (*lb_parts)[4 * v + 2] = sgn;
+      (*lb_parts)[4 * v + 3] = static_cast<T>(widx);
+    }
+  }
+}
+
+// dLoss/dw (accumulated into gw) and dLoss/dL (into gL) from gsoft = dLoss/dLambda_bar.
+void weighted_backward(const Graph& g, const double* L, const double* w, int Tsw,
+                       const double* gsoft, double* gw, double* gL) {
+  const int N = g.N, M = g.M, E = g.E;
+  std::vector<WStep<double>> tape;
+  std::vector<double> soft(N), parts;
+  weighted_forward<double>(g, L, w, Tsw, soft.data(), &tape, &parts);
+  std::vector<double> gQ(N, 0.0), gP(N, 0.0), gS(M, 0.0), gR(E, 0.0);
+  std::vector<int> last(N, -1);
+  // final state: the last check of every variable is the check of its last edge step
+  for (const auto& st : tape) last[st.v] = st.ci;
+  for (int v = 0; v < N; ++v) {  // flushed posterior, reversed
+    const double d = parts[4 * v], mag = parts[4 * v + 1], sgn = parts[4 * v + 2];
+    const int widx = static_cast<int>(parts[4 * v + 3]);
+    const double gl = gsoft[v];
+    gQ[v] += gl;
+    gw[widx] += gl * sgn * mag;
+    const double gd = gl * sgn * w[widx] * dphi_t<double>(std::fabs(d)) * (d < 0 ? -1.0 : 1.0);
+    gS[last[v]] += gd;
+    gP[v] -= gd;
+  }
+  // edge updates in reverse order; the adjoint of a check's S starts at its last use
+  double gSacc = 0.0;
+  int cur = -1;
+  for (size_t k = tape.size(); k-- > 0;) {
+    const WStep<double>& st = tape[k];
+    if (st.ci != cur) {   // reverse of S[ci] = sum of phi(|Q^new|) over the check
+      cur = st.ci;
+      gSacc = gS[cur];
+      gS[cur] = 0.0;
+    }
+    const int v = st.v;
+    const double gphn = gP[v] + gSacc;                          // phn = phi(|qn|)
+    const double gqn = gQ[v] + gphn * dphi_t<double>(std::fabs(st.qn)) * (st.qn < 0 ? -1.0 : 1.0);
+    const double glam = gqn;                                    // qn = lam - R[e]
+    gR[st.e] -= gqn;                                            // R[e] read
+    double gRn = glam;                                          // lam = Q + Rn
+    gQ[v] = glam;                                               // adjoint of the old Q*_v
+    gP[v] = 0.0;
+    if (st.ej >= 0) {
+      gRn += gR[st.ej];                                         // R[ej] = Rn (write)
+      gR[st.ej] = 0.0;
+      gw[st.widx] += gRn * st.sgn * st.mag;                     // Rn = sgn * w * mag
+      const double gd = gRn * st.sgn * st.w * dphi_t<double>(std::fabs(st.d)) *
+                        (st.d < 0 ? -1.0 : 1.0);
+      gS[st.cj] += gd;                                          // d = S[cj] - Ph[v]
+      gP[v] = -gd;
+    }
+  }
+  for (int v = 0; v < N; ++v) gL[v] += gQ[v];
+}
+
 bool build_graph(const int32_t* base, int mb, int nb, int Z, Graph& g) {
   if (!base || mb < 1 || nb < 1 || Z < 1) return false;
   for (int i = 0; i < mb * nb; ++i)
@@ -489,6 +628,8 @@ bool build_graph(const int32_t* base, int mb, int nb, int Z, Graph& g) {
   }
   g.N = nb * Z;
   g.M = mb * Z;
+  g.Z = Z;
+  g.mb = mb;
   g.cptr.assign(1, 0);
   g.cvar.clear();
   g.echk.clear();
@@ -652,6 +793,41 @@ int orc_cbp_trace_f64(const orc_code* c, const double* llr, int sweeps, double* 
     sig_out[m] = sg[m];
   }
   for (int e = 0; e < g.E; ++e) r_edge[e] = R[e];
+  return 0;
+}
+
+// Weighted CBP forward (T sweeps, no stop) on `batch` frames: soft = flushed posterior.
+int orc_weighted_f64(const orc_code* c, const double* llr, const double* w, int Tsw, int batch,
+                     double* soft) {
+  if (!c || Tsw < 1 || batch < 0) return -1;
+  for (int b = 0; b < batch; ++b)
+    weighted_forward<double>(c->g, llr + static_cast<int64_t>(b) * c->g.N, w, Tsw,
+                             soft + static_cast<int64_t>(b) * c->g.N, nullptr, nullptr);
+  return 0;
+}
+
+int orc_weighted_f32(const orc_code* c, const float* llr, const float* w, int Tsw, int batch,
+                     float* soft) {
+  if (!c || Tsw < 1 || batch < 0) return -1;
+  for (int b = 0; b < batch; ++b)
+    weighted_forward<float>(c->g, llr + static_cast<int64_t>(b) * c->g.N, w, Tsw,
+                            soft + static_cast<int64_t>(b) * c->g.N, nullptr, nullptr);
+  return 0;
+}
+
+// Reverse-mode adjoint of orc_weighted_f64: grad_w (T*mb, summed over the frames) and
+// grad_llr ([batch][N]) from grad_soft = dLoss/dsoft ([batch][N]).  Overwrites both.
+int orc_weighted_grad_f64(const orc_code* c, const double* llr, const double* w, int Tsw,
+                          int batch, const double* grad_soft, double* grad_w, double* grad_llr) {
+  if (!c || Tsw < 1 || batch < 0) return -1;
+  const int N = c->g.N;
+  std::fill(grad_w, grad_w + static_cast<size_t>(Tsw) * c->g.mb, 0.0);
+  for (int b = 0; b < batch; ++b) {
+    double* gl = grad_llr + static_cast<int64_t>(b) * N;
+    std::fill(gl, gl + N, 0.0);
+    weighted_backward(c->g, llr + static_cast<int64_t>(b) * N, w, Tsw,
+                      grad_soft + static_cast<int64_t>(b) * N, grad_w, gl);
+  }
   return 0;
 }
 

@@ -62,6 +62,12 @@ def lib():
                                          u8p, i32p, P, P, P, C.c_int]
             L.orc_cbp_trace_f64.restype = C.c_int
             L.orc_cbp_trace_f64.argtypes = [P, f64p, C.c_int, f64p, u8p, f64p, f64p]
+            L.orc_weighted_f64.restype = C.c_int
+            L.orc_weighted_f64.argtypes = [P, f64p, f64p, C.c_int, C.c_int, f64p]
+            L.orc_weighted_f32.restype = C.c_int
+            L.orc_weighted_f32.argtypes = [P, f32p, f32p, C.c_int, C.c_int, f32p]
+            L.orc_weighted_grad_f64.restype = C.c_int
+            L.orc_weighted_grad_f64.argtypes = [P, f64p, f64p, C.c_int, C.c_int, f64p, f64p, f64p]
             L.orc_phi_f32.argtypes = [f32p, f32p, C.c_int64]
             L.orc_phi_f64.argtypes = [f64p, f64p, C.c_int64]
             L.orc_phi_table_f32.restype = C.c_int
@@ -120,6 +126,28 @@ class OracleCode:
             raise ValueError(f"oracle decode failed ({rc})")
         return {"hard": hard, "iters": iters, "soft": sft, "flags": flags,
                 "counts": dict(zip(COUNTERS, counts.tolist()))}
+
+    def weighted(self, llr, w, T: int, precision: int = 64):
+        """Weighted CBP, T sweeps: flushed posterior [F, N].  w: [T, mb] scales."""
+        dt = np.float64 if precision == 64 else np.float32
+        llr = np.ascontiguousarray(np.asarray(llr, dtype=dt).reshape(-1, self.N))
+        w = np.ascontiguousarray(np.asarray(w, dtype=dt).reshape(-1))
+        out = np.zeros_like(llr)
+        fn = self._lib.orc_weighted_f64 if precision == 64 else self._lib.orc_weighted_f32
+        if fn(self._h, llr, w, int(T), llr.shape[0], out) != 0:
+            raise ValueError("weighted forward failed")
+        return out
+
+    def weighted_grad(self, llr, w, T: int, grad_soft):
+        """FP64 adjoint: (grad_w [T, mb] summed over frames, grad_llr [F, N])."""
+        llr = np.ascontiguousarray(np.asarray(llr, dtype=np.float64).reshape(-1, self.N))
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float64).reshape(-1))
+        gs = np.ascontiguousarray(np.asarray(grad_soft, dtype=np.float64).reshape(llr.shape))
+        gw = np.zeros_like(w)
+        gl = np.zeros_like(llr)
+        if self._lib.orc_weighted_grad_f64(self._h, llr, w, int(T), llr.shape[0], gs, gw, gl) != 0:
+            raise ValueError("weighted adjoint failed")
+        return gw.reshape(int(T), -1), gl
 
     def trace(self, llr, sweeps: int):
         """FP64 CBP on one frame for exactly ``sweeps`` sweeps: (S, sigma, Q per edge, R per edge)."""

@@ -24,7 +24,8 @@ STATUS = {0: "CBP_OK", -1: "CBP_EINVAL", -2: "CBP_ENOMEM", -3: "CBP_ECUDA",
 
 # Every symbol include/cbp.h declares (checked by the ABI test).
 EXPORTS = ("cbp_code_create", "cbp_code_destroy", "cbp_code_info", "cbp_workspace_bytes",
-           "cbp_launch_info", "cbp_decode", "cbp_decode_ex", "cbp_decode_noalloc", "cbp_phi",
+           "cbp_launch_info", "cbp_decode", "cbp_decode_ex", "cbp_grad_workspace_bytes",
+           "cbp_decode_weighted", "cbp_decode_grad", "cbp_decode_noalloc", "cbp_phi",
            "cbp_strerror")
 
 
@@ -66,6 +67,12 @@ def lib(build_if_needed: bool = True):
             L.cbp_decode.argtypes = [P, P, P, P, I, I, P, Z, P]
             L.cbp_decode_ex.restype = I
             L.cbp_decode_ex.argtypes = [P, P, P, P, I, I, P, Z, P, C.POINTER(_Opts)]
+            L.cbp_grad_workspace_bytes.restype = I
+            L.cbp_grad_workspace_bytes.argtypes = [P, I, I, I, C.POINTER(Z)]
+            L.cbp_decode_weighted.restype = I
+            L.cbp_decode_weighted.argtypes = [P, P, P, I, I, I, P, P, Z, P]
+            L.cbp_decode_grad.restype = I
+            L.cbp_decode_grad.argtypes = [P, P, P, I, I, I, P, P, P, P, Z, P]
             L.cbp_decode_noalloc.restype = I
             L.cbp_decode_noalloc.argtypes = [P, P, P, P, I, I, P]
             L.cbp_phi.restype = I
@@ -210,3 +217,52 @@ def unpack_bits(words: torch.Tensor, N: int) -> torch.Tensor:
     shifts = torch.arange(32, device=w.device, dtype=torch.int64)
     b = (w[:, :, None] >> shifts) & 1
     return b.reshape(w.shape[0], -1)[:, :N].to(torch.uint8)
+
+
+# ----------------------------------------------------------------------------- differentiable
+class _WeightedCBP(torch.autograd.Function):
+    """Weighted CBP as an autograd function: forward cbp_decode_weighted (checkpoints in a
+    workspace kept on the context), backward cbp_decode_grad."""
+
+    @staticmethod
+    def forward(ctx, llr, weights, code, T, ckpt_every):
+        llr = llr.contiguous()
+        w = weights.detach().contiguous().to(torch.float32)
+        B = llr.shape[0]
+        need = C.c_size_t()
+        _check("cbp_grad_workspace_bytes",
+               lib().cbp_grad_workspace_bytes(code._h, B, int(T), int(ckpt_every), C.byref(need)))
+        ws = torch.empty(max(need.value, 256), dtype=torch.uint8, device=llr.device)
+        soft = torch.empty_like(llr)
+        _check("cbp_decode_weighted",
+               lib().cbp_decode_weighted(code._h, llr.data_ptr(), w.data_ptr(), int(T),
+                                         int(ckpt_every), B, soft.data_ptr(), ws.data_ptr(),
+                                         ws.numel(), _stream_ptr()))
+        ctx.save_for_backward(llr, w)
+        ctx.ws, ctx.code, ctx.T, ctx.ckpt = ws, code, int(T), int(ckpt_every)
+        return soft
+
+    @staticmethod
+    def backward(ctx, grad_soft):
+        llr, w = ctx.saved_tensors
+        gs = grad_soft.contiguous().to(torch.float32)
+        gw = torch.empty_like(w)
+        gl = torch.empty_like(llr) if ctx.needs_input_grad[0] else None
+        B = llr.shape[0]
+        _check("cbp_decode_grad",
+               lib().cbp_decode_grad(ctx.code._h, llr.data_ptr(), w.data_ptr(), ctx.T, ctx.ckpt,
+                                     B, gs.data_ptr(), gw.data_ptr(),
+                                     gl.data_ptr() if gl is not None else None,
+                                     ctx.ws.data_ptr(), ctx.ws.numel(), _stream_ptr()))
+        ctx.ws = None
+        return gl, gw, None, None, None
+
+
+def weighted_cbp(code: Code, llr: torch.Tensor, weights: torch.Tensor, T: int,
+                 ckpt_every: int = 2) -> torch.Tensor:
+    """Differentiable weighted CBP: posterior LLRs [B, N] after T sweeps.
+
+    ``weights`` [T, mb] scale the B2V messages per sweep and base row of the sending
+    check (all ones = plain CBP with T sweeps).  Gradients flow to ``weights`` and
+    ``llr`` through the library's adjoint kernel."""
+    return _WeightedCBP.apply(llr, weights, code, int(T), int(ckpt_every))

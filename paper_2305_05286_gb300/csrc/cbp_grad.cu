@@ -1,0 +1,320 @@
+// Weighted CBP and its reverse-mode adjoint on sm_103a (the differentiable decoder).
+//
+// Forward (cbp_decode_weighted): T sweeps of CBP in log-tanh form, no stop, with the
+// B2V message of Eq. (s4e18) scaled by w[tau][b]: tau is the sweep in which the
+// predecessor check c_j formed its belief (this sweep if its base row comes earlier,
+// else the previous sweep), b is c_j's base row; R^new = sgn * (w * phi(|S_cj - phi_v|)).
+// The flushed posterior after sweep T (tau = T) is the output.  The state of every
+// frame at the start of each segment of `ckpt` sweeps is saved in the workspace.
+//
+// Backward (cbp_decode_grad): from dLoss/dsoft, the adjoint of the flush, then for the
+// segments in reverse: restore the segment's checkpoint, recompute its sweeps while
+// recording per edge update (d = |S_cj| - phi_v, sgn * phi(|d|), Q^new), and run the
+// sweeps backwards (base rows descending, a check's edges descending), propagating
+// adjoints of Q*_v, phi(|Q*_v|), S_c and the C2V slots, and accumulating dLoss/dw.
+// The adjoint of phi is the derivative of the evaluated cubic (phi_deriv).
+//
+// Layout: F frames per CTA, Z lanes per frame (lane z owns check r*Z + z); all per-frame
+// arrays live in the workspace, frame-major:
+//   state   Q*[N] | phi[N] | S[M] (sign bit = sgn Omega) | R[E] ([base entry][lane])
+//   adjoint gQ[N] | gP[N] | gS[M] | gR[E]
+//   nseg checkpoints of the state
+//   tape    d, sgn*mag, Q^new, each [ckpt][E]
+#include "cbp_internal.cuh"
+
+namespace cbp {
+namespace {
+
+__device__ __forceinline__ int mod_add(int a, int Z) { return a >= Z ? a - Z : a; }
+__device__ __forceinline__ uint32_t sign_bit(float x) { return __float_as_uint(x) >> 31; }
+
+struct Frame {
+  float *Q, *P, *S, *R;       // state
+  float *gQ, *gP, *gS, *gR;   // adjoint
+  float* ck;                  // checkpoints
+  float *td, *tm, *tq;        // tape
+};
+
+__device__ __forceinline__ Frame frame_view(const GParams& p, long long f) {
+  Frame fr;
+  float* b = p.ws + f * p.frame_floats;
+  fr.Q = b;
+  fr.P = b + p.N;
+  fr.S = b + 2 * p.N;
+  fr.R = b + 2 * p.N + p.M;
+  float* a = b + p.st_floats;
+  fr.gQ = a;
+  fr.gP = a + p.N;
+  fr.gS = a + 2 * p.N;
+  fr.gR = a + 2 * p.N + p.M;
+  fr.ck = b + 2 * p.st_floats;
+  float* tp = fr.ck + static_cast<long long>(p.nseg) * p.st_floats;
+  const long long te = static_cast<long long>(p.ckpt) * p.E;
+  fr.td = tp;
+  fr.tm = tp + te;
+  fr.tq = tp + 2 * te;
+  return fr;
+}
+
+struct Shared {
+  float4* tab;
+  BaseEdge* e;
+  int* rptr;
+  uint2* col;  // (last row | shift << 16)
+  float* gw;   // [T*mb]
+};
+
+__device__ Shared carve(unsigned char* smem, const GParams& p, bool load) {
+  Shared sh;
+  unsigned char* sp = smem;
+  sh.tab = reinterpret_cast<float4*>(sp);
+  sp += sizeof(float4) * kPhiSegments;
+  sh.e = reinterpret_cast<BaseEdge*>(sp);
+  sp += sizeof(BaseEdge) * p.nnzb;
+  sh.rptr = reinterpret_cast<int*>(sp);
+  sp += sizeof(int) * ((p.mb + 1 + 3) & ~3);
+  sh.col = reinterpret_cast<uint2*>(sp);
+  sp += sizeof(uint2) * ((p.nb + 1) & ~1);
+  sh.gw = reinterpret_cast<float*>(sp);
+  if (load) {
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kPhiSegments; i += blockDim.x) sh.tab[i] = p.phi_tab[i];
+    for (int i = tid; i < p.nnzb; i += blockDim.x) sh.e[i] = p.edges[i];
+    for (int i = tid; i <= p.mb; i += blockDim.x) sh.rptr[i] = p.rptr[i];
+    for (int c = tid; c < p.nb; c += blockDim.x) {
+      const ColEntry ce = p.cols[p.cptr[c + 1] - 1];
+      sh.col[c] = make_uint2(uint32_t(ce.r) | (uint32_t(ce.s) << 16), 0u);
+    }
+    for (int i = tid; i < p.T * p.mb; i += blockDim.x) sh.gw[i] = 0.0f;
+  }
+  return sh;
+}
+
+// Copy a frame's state to / from a checkpoint (the Z lanes of the frame share the work).
+__device__ __forceinline__ void copy_state(float* dst, const float* src, long long n, int z,
+                                           int Z) {
+  for (long long i = z; i < n; i += Z) dst[i] = src[i];
+}
+
+// Forward sweeps t0..t1 (1-based, inclusive) of one frame, optionally recording the tape.
+__device__ void forward_sweeps(const GParams& p, const Shared& sh, const Frame& fr, bool act,
+                               int z, int t0, int t1, bool tape) {
+  const int Z = p.Z;
+  for (int t = t0; t <= t1; ++t) {
+    const int ts = t - t0;
+    for (int r = 0; r < p.mb; ++r) {
+      if (act) {
+        float Sacc = 0.0f;
+        uint32_t sig = 0;
+        for (int k = sh.rptr[r]; k < sh.rptr[r + 1]; ++k) {
+          const BaseEdge be = sh.e[k];
+          const int zv = mod_add(z + be.s, Z);
+          const int v = be.c * Z + zv;
+          const bool self = be.flags & kSelf;
+          const float q = fr.Q[v];
+          float Rn = 0.0f, d = 0.0f, smag = 0.0f;
+          if (!(t == 1 && (be.flags & kFirst))) {
+            int zj = zv - be.ps;
+            zj = zj < 0 ? zj + Z : zj;
+            const float Sj = fr.S[be.pr * Z + zj];
+            d = __fsub_rn(fabsf(Sj), fr.P[v]);
+            const float mag = phi_eval(fabsf(d), p.phi_xlo, sh.tab);
+            const int tau = (be.pr < r) ? t : t - 1;
+            const float wm = __fmul_rn(p.w[(tau - 1) * p.mb + be.pr], mag);
+            const bool neg = sign_bit(Sj) ^ (q < 0.0f);
+            Rn = neg ? -wm : wm;
+            smag = neg ? -mag : mag;
+            if (!self) fr.R[be.pe * Z + zj] = Rn;
+          }
+          const float rold = self ? Rn : (t > 1 ? fr.R[k * Z + z] : 0.0f);
+          const float qn = __fsub_rn(__fadd_rn(q, Rn), rold);
+          const float phn = phi_eval(fabsf(qn), p.phi_xlo, sh.tab);
+          Sacc = __fadd_rn(Sacc, phn);
+          sig ^= (qn < 0.0f);
+          fr.Q[v] = qn;
+          fr.P[v] = phn;
+          if (tape) {
+            const long long o = static_cast<long long>(ts) * p.E + k * Z + z;
+            fr.td[o] = d;
+            fr.tm[o] = smag;
+            fr.tq[o] = qn;
+          }
+        }
+        fr.S[r * Z + z] = sig ? -Sacc : Sacc;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Warp-sum `x` and add it to sh.gw[idx] (every lane of the warp passes the same idx).
+__device__ __forceinline__ void add_gw(const Shared& sh, int idx, float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  if ((threadIdx.x & 31) == 0 && x != 0.0f) atomicAdd(sh.gw + idx, x);
+}
+
+__global__ void __launch_bounds__(512) weighted_forward_kernel(const GParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Shared sh = carve(smem, p, true);
+  const int Z = p.Z;
+  const int f = threadIdx.x / Z, z = threadIdx.x - f * Z;
+  const long long frame = static_cast<long long>(blockIdx.x) * p.F + f;
+  const bool act = f < p.F && frame < p.batch;
+  const Frame fr = frame_view(p, act ? frame : 0);
+  __syncthreads();
+  if (act) {
+    const float* L = p.llr + frame * p.N;
+    for (int i = z; i < p.N; i += Z) fr.Q[i] = L[i];  // Eq. (s4e15)
+  }
+  for (int s = 0; s < p.nseg; ++s) {
+    const int t0 = s * p.ckpt + 1, t1 = min(p.T, (s + 1) * p.ckpt);
+    __syncthreads();
+    if (act) copy_state(fr.ck + static_cast<long long>(s) * p.st_floats, fr.Q, p.st_floats, z, Z);
+    __syncthreads();
+    forward_sweeps(p, sh, fr, act, z, t0, t1, false);
+  }
+  if (act) {  // flushed posterior, tau = T
+    for (int c = 0; c < p.nb; ++c) {
+      const uint32_t l = sh.col[c].x;
+      const int rk = int(l & 0xffff), sk = int(l >> 16);
+      int zk = z - sk;
+      zk = zk < 0 ? zk + Z : zk;
+      const int v = c * Z + z;
+      const float Sk = fr.S[rk * Z + zk];
+      const float q = fr.Q[v];
+      const float mag = phi_eval(fabsf(__fsub_rn(fabsf(Sk), fr.P[v])), p.phi_xlo, sh.tab);
+      const float wm = __fmul_rn(p.w[(p.T - 1) * p.mb + rk], mag);
+      p.soft[frame * p.N + v] = __fadd_rn(q, (sign_bit(Sk) ^ (q < 0.0f)) ? -wm : wm);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(512) weighted_backward_kernel(const GParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Shared sh = carve(smem, p, true);
+  const int Z = p.Z;
+  const int f = threadIdx.x / Z, z = threadIdx.x - f * Z;
+  const long long frame = static_cast<long long>(blockIdx.x) * p.F + f;
+  const bool act = f < p.F && frame < p.batch;
+  const Frame fr = frame_view(p, act ? frame : 0);
+  const float xlo = p.phi_xlo;
+  if (act)
+    for (long long i = z; i < p.st_floats; i += Z) fr.gQ[i] = 0.0f;  // all adjoints
+  __syncthreads();
+  // ---- adjoint of the flushed posterior (the state is the final one of the forward)
+  for (int r = 0; r < p.mb; ++r) {
+    for (int k = sh.rptr[r]; k < sh.rptr[r + 1]; ++k) {
+      const BaseEdge be = sh.e[k];
+      float gwx = 0.0f;
+      if (act && (be.flags & kLast)) {
+        const int v = be.c * Z + mod_add(z + be.s, Z);
+        const int m = r * Z + z;
+        const float Sm = fr.S[m], q = fr.Q[v];
+        const float d = __fsub_rn(fabsf(Sm), fr.P[v]);
+        const float mag = phi_eval(fabsf(d), xlo, sh.tab);
+        const float sgn = (sign_bit(Sm) ^ (q < 0.0f)) ? -1.0f : 1.0f;
+        const float w = p.w[(p.T - 1) * p.mb + r];
+        const float gl = p.gsoft[frame * p.N + v];
+        fr.gQ[v] = gl;
+        gwx = gl * sgn * mag;
+        const float gd = gl * sgn * w * phi_deriv(fabsf(d), xlo, sh.tab) * (d < 0.0f ? -1.0f : 1.0f);
+        fr.gS[m] += gd;
+        fr.gP[v] = -gd;
+      }
+      if (be.flags & kLast) add_gw(sh, (p.T - 1) * p.mb + r, gwx);
+    }
+  }
+  __syncthreads();
+  // ---- segments in reverse: recompute with the tape, then sweep backwards
+  for (int s = p.nseg - 1; s >= 0; --s) {
+    const int t0 = s * p.ckpt + 1, t1 = min(p.T, (s + 1) * p.ckpt);
+    if (act) copy_state(fr.Q, fr.ck + static_cast<long long>(s) * p.st_floats, p.st_floats, z, Z);
+    __syncthreads();
+    forward_sweeps(p, sh, fr, act, z, t0, t1, true);
+    for (int t = t1; t >= t0; --t) {
+      const int ts = t - t0;
+      for (int r = p.mb - 1; r >= 0; --r) {
+        const int m = r * Z + z;
+        float gSacc = 0.0f;
+        if (act) {
+          gSacc = fr.gS[m];
+          fr.gS[m] = 0.0f;
+        }
+        for (int k = sh.rptr[r + 1] - 1; k >= sh.rptr[r]; --k) {
+          const BaseEdge be = sh.e[k];
+          const bool first = (t == 1) && (be.flags & kFirst);
+          const int tau = (be.pr < r) ? t : t - 1;
+          float gwx = 0.0f;
+          if (act) {
+            const int zv = mod_add(z + be.s, Z);
+            const int v = be.c * Z + zv;
+            const bool self = be.flags & kSelf;
+            const long long o = static_cast<long long>(ts) * p.E + k * Z + z;
+            const float d = fr.td[o], smag = fr.tm[o], qn = fr.tq[o];
+            // phn = phi(|qn|) feeds phi_v and the sum S of this check
+            const float gphn = fr.gP[v] + gSacc;
+            const float gqn = fr.gQ[v] + gphn * phi_deriv(fabsf(qn), xlo, sh.tab) *
+                                             (qn < 0.0f ? -1.0f : 1.0f);
+            fr.gR[k * Z + z] -= gqn;  // qn = (Q + Rn) - R[own]
+            float gRn = gqn;           // and Lambda = Q + Rn
+            fr.gQ[v] = gqn;
+            fr.gP[v] = 0.0f;
+            if (!first) {
+              int zj = zv - be.ps;
+              zj = zj < 0 ? zj + Z : zj;
+              const int slot = self ? k * Z + z : be.pe * Z + zj;
+              gRn += fr.gR[slot];      // R[slot] = Rn
+              fr.gR[slot] = 0.0f;
+              gwx = gRn * smag;        // Rn = sgn * w * mag
+              const float w = p.w[(tau - 1) * p.mb + be.pr];
+              const float sgn = smag < 0.0f ? -1.0f : 1.0f;
+              const float gd = gRn * sgn * w * phi_deriv(fabsf(d), xlo, sh.tab) *
+                               (d < 0.0f ? -1.0f : 1.0f);
+              atomicAdd(fr.gS + be.pr * Z + zj, gd);  // d = |S_cj| - phi_v
+              fr.gP[v] = -gd;
+            }
+          }
+          if (!first) add_gw(sh, (tau - 1) * p.mb + be.pr, gwx);
+        }
+        __syncthreads();
+      }
+    }
+  }
+  if (act && p.gllr)
+    for (int i = z; i < p.N; i += Z) p.gllr[frame * p.N + i] = fr.gQ[i];  // Q* = L
+  __syncthreads();
+  for (int i = threadIdx.x; i < p.T * p.mb; i += blockDim.x)
+    if (sh.gw[i] != 0.0f) atomicAdd(p.gw + i, sh.gw[i]);
+}
+
+}  // namespace
+
+size_t grad_frame_floats(int N, int M, int E, int T, int ckpt) {
+  const size_t st = (2 * static_cast<size_t>(N) + M + E + 3) & ~static_cast<size_t>(3);
+  const size_t nseg = (T + ckpt - 1) / ckpt;
+  const size_t f = 2 * st + nseg * st + 3 * static_cast<size_t>(ckpt) * E;
+  return (f + 63) & ~static_cast<size_t>(63);
+}
+
+cudaError_t grad_set_smem(int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(weighted_forward_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(weighted_backward_kernel,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t launch_weighted_forward(const GParams& p, int grid, int threads, size_t smem,
+                                    cudaStream_t st) {
+  weighted_forward_kernel<<<grid, threads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_weighted_backward(const GParams& p, int grid, int threads, size_t smem,
+                                     cudaStream_t st) {
+  weighted_backward_kernel<<<grid, threads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace cbp

@@ -86,6 +86,7 @@ int device_init(int dev, DeviceInfo** out) {
                            {ALG_LBP_NMS, false, 1}, {ALG_FBP_SP, false, 1}};
     for (const Variant& v : all)
       if (decoder_set_smem(v, d.smem_optin) != cudaSuccess) return CBP_ECUDA;
+    if (grad_set_smem(d.smem_optin) != cudaSuccess) return CBP_ECUDA;
     d.tab = static_cast<float4*>(addr);
     d.xlo = xlo;
     d.ready = true;
@@ -419,7 +420,8 @@ int cbp_code_create(const int32_t* base, int mb, int nb, int Z, cbp_code_t** out
       e.pr = static_cast<uint16_t>(pr);
       e.ps = static_cast<uint16_t>(base[pr * nb + c]);
       e.pe = static_cast<uint16_t>(idx[pr * nb + c]);
-      e.flags = static_cast<uint16_t>((k == 0 ? kFirst : 0) | (w == 1 ? kSelf : 0));
+      e.flags = static_cast<uint16_t>((k == 0 ? kFirst : 0) | (w == 1 ? kSelf : 0) |
+                                      (k == w - 1 ? kLast : 0));
       e.pad = kind_idx;
       ColEntry ce{};
       ce.r = static_cast<uint16_t>(r);
@@ -606,6 +608,118 @@ int cbp_decode(const cbp_code_t* c, const float* llr, uint32_t* hard_out, int32_
                cbp_stream_t stream) {
   return cbp_decode_ex(c, llr, hard_out, iters_out, max_iter, batch, workspace,
                        workspace_bytes, stream, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Weighted CBP (differentiable decoder)
+// ---------------------------------------------------------------------------
+namespace {
+
+int grad_setup(const cbp_code_t* c, int batch, int T, int ckpt, GParams* p, int* grid,
+               int* threads, size_t* smem, size_t* ws_bytes, DeviceInfo** dio) {
+  if (!c || batch < 0 || T < 1 || ckpt < 1 || ckpt > T) return CBP_EINVAL;
+  if (c->Z > 512) return CBP_EUNSUPPORTED;
+  DeviceInfo* di = nullptr;
+  int dev = 0;
+  if (int rc = current_device(&di, &dev)) return rc;
+  if (dev != c->dev) return CBP_EDEVICE;
+  const size_t ff = grad_frame_floats(c->N, c->M, c->E, T, ckpt);
+  *ws_bytes = ff * sizeof(float) * static_cast<size_t>(batch);
+  const size_t sm = sizeof(float4) * kPhiSegments + sizeof(BaseEdge) * c->nnzb +
+                    sizeof(int) * ((c->mb + 1 + 3) & ~3) + sizeof(uint2) * ((c->nb + 1) & ~1) +
+                    sizeof(float) * static_cast<size_t>(T) * c->mb;
+  if (sm > static_cast<size_t>(di->smem_optin)) return CBP_EUNSUPPORTED;
+  const int F = std::max(1, 256 / c->Z);
+  *threads = (F * c->Z + 31) / 32 * 32;
+  *grid = static_cast<int>((static_cast<long long>(batch) + F - 1) / F);
+  *smem = sm;
+  GParams q{};
+  q.edges = c->d.edges;
+  q.rptr = c->d.rptr;
+  q.cols = c->d.cols;
+  q.cptr = c->d.cptr;
+  q.phi_tab = di->tab;
+  q.phi_xlo = di->xlo;
+  q.Z = c->Z;
+  q.mb = c->mb;
+  q.nb = c->nb;
+  q.nnzb = c->nnzb;
+  q.N = c->N;
+  q.M = c->M;
+  q.E = c->E;
+  q.batch = batch;
+  q.T = T;
+  q.ckpt = ckpt;
+  q.nseg = (T + ckpt - 1) / ckpt;
+  q.F = F;
+  q.frame_floats = static_cast<long long>(ff);
+  q.st_floats = static_cast<long long>((2 * static_cast<size_t>(c->N) + c->M + c->E + 3) & ~static_cast<size_t>(3));
+  *p = q;
+  if (dio) *dio = di;
+  return CBP_OK;
+}
+
+}  // namespace
+
+int cbp_grad_workspace_bytes(const cbp_code_t* c, int batch, int T, int ckpt_every,
+                             size_t* bytes) {
+  if (!bytes) return CBP_EINVAL;
+  GParams p;
+  int grid, threads;
+  size_t smem;
+  return grad_setup(c, batch, T, ckpt_every, &p, &grid, &threads, &smem, bytes, nullptr);
+}
+
+int cbp_decode_weighted(const cbp_code_t* c, const float* llr, const float* weights, int T,
+                        int ckpt_every, int batch, float* soft_out, void* workspace,
+                        size_t workspace_bytes, cbp_stream_t stream) {
+  GParams p;
+  int grid, threads;
+  size_t smem, need;
+  if (int rc = grad_setup(c, batch, T, ckpt_every, &p, &grid, &threads, &smem, &need, nullptr))
+    return rc;
+  if (batch == 0) return CBP_OK;
+  if (!llr || !weights || !soft_out || !workspace) return CBP_EINVAL;
+  if (!aligned(llr, 4) || !aligned(weights, 4) || !aligned(soft_out, 4) || !aligned(workspace, 256))
+    return CBP_EINVAL;
+  if (workspace_bytes < need) return CBP_EWORKSPACE;
+  p.llr = llr;
+  p.w = weights;
+  p.soft = soft_out;
+  p.ws = static_cast<float*>(workspace);
+  return launch_weighted_forward(p, grid, threads, smem, reinterpret_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? CBP_OK
+             : CBP_ECUDA;
+}
+
+int cbp_decode_grad(const cbp_code_t* c, const float* llr, const float* weights, int T,
+                    int ckpt_every, int batch, const float* grad_soft, float* grad_weights,
+                    float* grad_llr, void* workspace, size_t workspace_bytes,
+                    cbp_stream_t stream) {
+  GParams p;
+  int grid, threads;
+  size_t smem, need;
+  if (int rc = grad_setup(c, batch, T, ckpt_every, &p, &grid, &threads, &smem, &need, nullptr))
+    return rc;
+  if (!grad_weights || !aligned(grad_weights, 4)) return CBP_EINVAL;
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(grad_weights, 0, sizeof(float) * static_cast<size_t>(T) * c->mb, st) !=
+      cudaSuccess)
+    return CBP_ECUDA;
+  if (batch == 0) return CBP_OK;
+  if (!llr || !weights || !grad_soft || !workspace) return CBP_EINVAL;
+  if (!aligned(llr, 4) || !aligned(weights, 4) || !aligned(grad_soft, 4) ||
+      !aligned(workspace, 256) || (grad_llr && !aligned(grad_llr, 4)))
+    return CBP_EINVAL;
+  if (workspace_bytes < need) return CBP_EWORKSPACE;
+  p.llr = llr;
+  p.w = weights;
+  p.gsoft = grad_soft;
+  p.gw = grad_weights;
+  p.gllr = grad_llr;
+  p.ws = static_cast<float*>(workspace);
+  return launch_weighted_backward(p, grid, threads, smem, st) == cudaSuccess ? CBP_OK : CBP_ECUDA;
 }
 
 // ---------------------------------------------------------------------------

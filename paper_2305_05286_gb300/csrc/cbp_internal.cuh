@@ -45,6 +45,27 @@ __device__ __forceinline__ float phi_eval(float x, float xlo, const float4* __re
   return __fmaf_rn(p, t, c.x);
 }
 
+// Derivative of phi_eval: the derivative of the cubic of the centre's segment,
+// c1 + t (2 c2 + 3 c3 t), times dt/dx (2^-e below 2, 16 above); 0 where the clamp holds.
+__device__ __forceinline__ float phi_deriv(float x, float xlo, const float4* __restrict__ tab) {
+  const bool inside = x >= xlo && x <= 30.0f;
+  x = fminf(fmaxf(x, xlo), 30.0f);
+  const uint32_t cb = (__float_as_uint(x) + 0x20000u) & 0xFFFC0000u;
+  const float inv = __uint_as_float(0x7F000000u - (cb & 0x7F800000u));
+  const float tl = __fmul_rn(__fsub_rn(x, __uint_as_float(cb)), inv);
+  constexpr float kMagic = 12582912.0f;
+  const float y = __fmaf_rn(x, 16.0f, kMagic);
+  const float tu = __fmaf_rn(x, 16.0f, -__fsub_rn(y, kMagic));
+  const bool lo = x < 2.0f;
+  const float t = lo ? tl : tu;
+  const int i = lo ? static_cast<int>(cb >> 18) - kPhiLogBase
+                   : static_cast<int>(__float_as_uint(y) - __float_as_uint(kMagic)) +
+                         (kPhiLogCount - 32);
+  const float4 c = tab[i];
+  const float dp = __fmaf_rn(__fmaf_rn(3.0f * c.w, t, 2.0f * c.z), t, c.y);
+  return inside ? dp * (lo ? inv : 16.0f) : 0.0f;
+}
+
 // ----------------------------------------------------------------------------
 // Code tables (built on the host by cbp_code_create).
 // ----------------------------------------------------------------------------
@@ -59,7 +80,8 @@ struct BaseEdge {
   uint32_t pad;    // low 16 bits: index of column c among the columns of its kind
                    // (weight >= 2 columns, or weight-1 columns)
 };
-constexpr uint16_t kFirst = 1, kSelf = 2;
+// kLast: r is the last row of column c (the check a flushed posterior reads).
+constexpr uint16_t kFirst = 1, kSelf = 2, kLast = 16;
 
 // Column-major view: the rows of column c in ascending order (flooding posterior).
 struct ColEntry {
@@ -133,6 +155,32 @@ void* minsum_kernel_ptr(int alg, bool chk_shared);          // cbp_minsum.cu
 void* flood_kernel_ptr();              // cbp_flood.cu
 cudaError_t launch_phi(const float* x, float* y, long long n, const float4* tab, float xlo,
                        cudaStream_t st);
+
+// Weighted CBP (differentiable decoder), cbp_grad.cu.
+struct GParams {
+  const float* llr;
+  const float* w;        // [T][mb]
+  float* soft;           // forward output [batch][N]
+  const float* gsoft;    // backward input [batch][N]
+  float* gw;             // [T][mb], accumulated
+  float* gllr;           // [batch][N] or null
+  float* ws;
+  const BaseEdge* edges;
+  const int* rptr;
+  const ColEntry* cols;
+  const int* cptr;
+  const float4* phi_tab;
+  float phi_xlo;
+  int Z, mb, nb, nnzb, N, M, E;
+  int batch, T, ckpt, nseg, F;
+  long long frame_floats, st_floats;
+};
+size_t grad_frame_floats(int N, int M, int E, int T, int ckpt);
+cudaError_t launch_weighted_forward(const GParams& p, int grid, int threads, size_t smem,
+                                    cudaStream_t st);
+cudaError_t launch_weighted_backward(const GParams& p, int grid, int threads, size_t smem,
+                                     cudaStream_t st);
+cudaError_t grad_set_smem(int bytes);
 
 constexpr int kMaxDeg = 32;     // row-degree limit of the two-pass (pooled) comparators
 constexpr int kMaxDegCbpMs = 64;  // CBP min-sum: one sign bit per edge in a 64-bit mask
