@@ -361,6 +361,79 @@ def run_sweep(args):
         del llr, cw
 
 
+def run_learned(args):
+    """Learned-weight CBP on the 2304-bit code (12x24 base, Z=96, seed 4): train the
+    T x mb B2V scales (init 1.0) with Adam on fresh frames at Eb/N0 ~ U[1, 3] dB, then
+    compare FER and decoded Gbit/s against plain CBP and layered min-sum at T sweeps."""
+    import torch
+
+    from paper_2305_05286_gb300 import cbp
+    from paper_2305_05286_gb300 import inputs as I
+
+    qc = I.code_2304()
+    code = cbp.Code.from_qc(qc)
+    K = (qc.nb - qc.mb) * qc.Z
+    T, B = 10, args.train_frames
+    w = torch.ones((T, qc.mb), device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([w], lr=args.lr)
+    g = torch.Generator(device="cuda").manual_seed(5000)
+    t0 = time.perf_counter()
+    losses = []
+    for step in range(args.train_steps):
+        ebn0 = 1.0 + 2.0 * torch.rand(B, generator=g, device="cuda")
+        llr, cw = I.make_frames_torch(qc, B, ebn0, seed=5000 + step)
+        soft = cbp.weighted_cbp(code, llr, w, T, 2)
+        loss = torch.nn.functional.binary_cross_entropy_with_logits(-soft, cw.float())
+        opt.zero_grad(set_to_none=True)
+        loss.backward()
+        opt.step()
+        if step % 50 == 0 or step == args.train_steps - 1:
+            losses.append((step, float(loss.item())))
+            print(json.dumps({"train_step": step, "loss": losses[-1][1],
+                              "elapsed_s": time.perf_counter() - t0}), flush=True)
+    train_s = time.perf_counter() - t0
+    wl = w.detach().clone()
+    ones = torch.ones_like(wl)
+    stream = torch.cuda.current_stream()
+    rows = []
+    chunk = min(args.eval_frames, 16384)
+    for pi, e in enumerate((1.5, 2.0, 2.5)):
+        stats = {k: [0, 0, 0.0] for k in ("learned", "cbp_T", "cbp_stop", "lbp_nms")}
+        done = 0
+        while done < args.eval_frames:
+            n = min(chunk, args.eval_frames - done)
+            llr, cw = I.make_frames_torch(qc, n, e, seed=6000 + 1000 * pi + done // chunk)
+            for name in stats:
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                with torch.no_grad():
+                    if name in ("learned", "cbp_T"):
+                        soft = cbp.weighted_cbp(code, llr, wl if name == "learned" else ones, T, 5)
+                        bits = (soft < 0).to(torch.uint8)
+                    else:
+                        hard, iters, _ = code.decode(llr, max_iter=T,
+                                                     alg="cbp_sp" if name == "cbp_stop" else "lbp_nms")
+                        bits = cbp.unpack_bits(hard, qc.N)
+                ev1.record(stream)
+                ev1.synchronize()
+                st = stats[name]
+                st[0] += int((bits != cw).any(dim=1).sum().item())
+                st[1] += int((bits != cw).sum().item())
+                st[2] += ev0.elapsed_time(ev1) / 1e3
+            done += n
+        for name, (fe, be, secs) in stats.items():
+            row = {"ebn0_db": e, "decoder": name, "frames": done, "fer": fe / done,
+                   "ber": be / (done * qc.N), "gbps": K * done / secs / 1e9,
+                   "sweeps": T if name != "cbp_stop" and name != "lbp_nms" else f"<= {T}"}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+    print(json.dumps({"learned_weights": wl.cpu().numpy().round(4).tolist(),
+                      "train_steps": args.train_steps, "train_frames": B,
+                      "train_seconds": train_s, "loss_first_last": [losses[0], losses[-1]]}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -372,6 +445,11 @@ def main():
     ap.add_argument("--frames", type=int, default=FRAMES)
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--sweep-frames", type=int, default=16384)
+    ap.add_argument("--learned", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=2000)
+    ap.add_argument("--train-frames", type=int, default=8192)
+    ap.add_argument("--eval-frames", type=int, default=1_000_000)
+    ap.add_argument("--lr", type=float, default=0.01)
     ap.add_argument("--sweep-lo", type=float, default=0.0)
     ap.add_argument("--sweep-hi", type=float, default=2.0)
     ap.add_argument("--no-comparators", action="store_true")
@@ -399,6 +477,8 @@ def main():
         run_reference(args, rank)
     elif args.sweep:
         run_sweep(args)
+    elif args.learned:
+        run_learned(args)
     else:
         run_ours(args, rank, world, dist)
     if dist:

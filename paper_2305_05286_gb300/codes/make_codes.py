@@ -29,5 +29,24 @@ def main():
                      "to two entries in the core rows 0-3.")
 
 
+# Mixed batch: eight codes of the same dual-diagonal structure, (Z, rate, mb x nb).
+MIXED = [(16, "1/3", 16, 24), (32, "2/5", 15, 25), (64, "1/2", 12, 24), (96, "2/3", 8, 24),
+         (128, "3/4", 6, 24), (192, "5/6", 4, 24), (256, "8/9", 3, 27), (384, "1/2", 12, 24)]
+
+
+def mixed_name(i):
+    Z, _, mb, nb = MIXED[i]
+    return f"mix{i}_{mb}x{nb}_z{Z}"
+
+
+def make_mixed():
+    for i, (Z, rate, mb, nb) in enumerate(MIXED):
+        b = inputs.make_dual_diagonal_code(mb=mb, nb=nb, Z=Z, col_weight=min(3, mb), seed=300 + i)
+        inputs.save_base(os.path.join(HERE, mixed_name(i) + ".txt"), b, Z,
+                         f"Mixed-batch code {i}: {mb}x{nb} base, Z={Z}, rate {rate}, seed {300 + i}.\n"
+                         "Info columns: weight min(3, mb), shifts uniform, 4-cycles rejected;\n"
+                         "parity columns: lower bidiagonal of identity blocks.")
+
+
 if __name__ == "__main__":
     main()

@@ -265,6 +265,13 @@ def code_2304() -> QCCode:
     return load_code("qc_12x24_z96_seed4")
 
 
+def mixed_codes() -> list[QCCode]:
+    """The eight codes of the mixed batch: Z = 16 ... 384, rates 1/3 ... 8/9."""
+    names = ["mix0_16x24_z16", "mix1_15x25_z32", "mix2_12x24_z64", "mix3_8x24_z96",
+             "mix4_6x24_z128", "mix5_4x24_z192", "mix6_3x27_z256", "mix7_12x24_z384"]
+    return [load_code(n) for n in names]
+
+
 def relift(code: QCCode, Z: int) -> QCCode:
     """Same base graph lifted by a smaller Z (shifts taken mod Z)."""
     b = code.base.copy()
