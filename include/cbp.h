@@ -188,6 +188,69 @@ int cbp_decode_grad(const cbp_code_t* code, const float* llr, const float* weigh
 int cbp_decode_noalloc(const cbp_code_t* code, const float* llr, uint32_t* hard_out,
                        int32_t* iters_out, int max_iter, int batch, cbp_stream_t stream);
 
+/* ---- Several codes in one launch (CBP log-tanh form, Sec. IV) -----------------------
+ * A receiver that serves several QC-LDPC codes at once (different lifting sizes Z,
+ * rates, batch sizes) decodes them all in one persistent launch.  Each item names a
+ * code handle and its own device buffers (the layout of cbp_decode).  The frames of
+ * every item are cut into chunks of whole lane-group rounds; the launch's CTAs take
+ * chunks from a work counter until none is left, the heaviest items first, so a small
+ * item rides along with a large one without a launch of its own.  The decoding of each
+ * frame is bit-identical to cbp_decode_ex(CBP_ALG_CBP_SP) of the same frame with the
+ * same stop mode.  The paper decodes one code at a time; this is a deployment feature.
+ *
+ * Items (at most CBP_MULTI_MAX_ITEMS, all codes on the current device):
+ *   code       handle;  llr, hard_out, iters_out, batch: as for cbp_decode
+ *              (batch 0 is allowed and decodes nothing for that item)
+ * Options (NULL = defaults; zero-initialise then set):
+ *   frames_per_group  1 or 2 frames interleaved per lane group (0 = 1)
+ *   chk_shared        1: check beliefs in shared memory, 0: in the workspace, -1 or
+ *                     any other value: the library picks (shared when every code fits)
+ *   threads           threads per CTA, a multiple of 32 up to 768 (fpt 1) or 384
+ *                     (fpt 2); every code's Z must be <= threads (0 = the maximum)
+ *   ctas_per_sm       CTAs resident per SM the shared-memory split aims at (0 = 1)
+ *   rounds_per_chunk  frame rounds of a CTA's lane groups per chunk (0 = 4)
+ *   stop_mode         cbp_stop (0 = CBP_STOP_SYNDROME)
+ * The workspace holds a work counter (the call zeroes it with cudaMemsetAsync on
+ * `stream` before the launch, so the call can be captured into a CUDA graph) and the
+ * per-CTA decoder state.  Errors: CBP_EINVAL (bad pointers, alignment, options,
+ * more than CBP_MULTI_MAX_ITEMS items), CBP_EDEVICE (a code of another device),
+ * CBP_EUNSUPPORTED (a code that does not fit the CTA shape), CBP_EWORKSPACE. */
+#define CBP_MULTI_MAX_ITEMS 8
+
+typedef struct cbp_multi_item {
+  const cbp_code_t* code;
+  const float* llr;
+  uint32_t* hard_out;
+  int32_t* iters_out;
+  int batch;
+} cbp_multi_item_t;
+
+typedef struct cbp_multi_opts {
+  int frames_per_group;
+  int chk_shared;
+  int threads;
+  int ctas_per_sm;
+  int rounds_per_chunk;
+  int stop_mode;
+} cbp_multi_opts_t;
+
+/* Bytes of workspace cbp_decode_multi needs for these items and options. */
+int cbp_multi_workspace_bytes(const cbp_multi_item_t* items, int n_items,
+                              const cbp_multi_opts_t* opts, size_t* bytes);
+
+/* The launch cbp_decode_multi would use: info[0] CTAs, info[1] threads per CTA,
+ * info[2] dynamic shared bytes per CTA, info[3] CTAs resident per SM, info[4] chunks,
+ * info[5] 1 if check beliefs are in shared memory, info[6] frames per lane group,
+ * info[7] unused (0).  `info` is a host array of 8 ints. */
+int cbp_multi_launch_info(const cbp_multi_item_t* items, int n_items,
+                          const cbp_multi_opts_t* opts, int* info);
+
+/* Decode every item's frames in one launch on `stream` (asynchronous; nothing is
+ * allocated).  max_iter >= 1 sweeps at most for every frame. */
+int cbp_decode_multi(const cbp_multi_item_t* items, int n_items, int max_iter,
+                     void* workspace, size_t workspace_bytes, cbp_stream_t stream,
+                     const cbp_multi_opts_t* opts);
+
 /* Evaluate the library's phi (Eq. s2e5, the clamped FP32 form used by the decoders)
  * on n device values: y[i] = phi(x[i]).  x, y device, 4-byte aligned, n >= 0. */
 int cbp_phi(const float* x, float* y, int64_t n, cbp_stream_t stream);

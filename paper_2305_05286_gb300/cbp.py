@@ -25,8 +25,10 @@ STATUS = {0: "CBP_OK", -1: "CBP_EINVAL", -2: "CBP_ENOMEM", -3: "CBP_ECUDA",
 # Every symbol include/cbp.h declares (checked by the ABI test).
 EXPORTS = ("cbp_code_create", "cbp_code_destroy", "cbp_code_info", "cbp_workspace_bytes",
            "cbp_launch_info", "cbp_decode", "cbp_decode_ex", "cbp_grad_workspace_bytes",
-           "cbp_decode_weighted", "cbp_decode_grad", "cbp_decode_noalloc", "cbp_phi",
+           "cbp_decode_weighted", "cbp_decode_grad", "cbp_decode_noalloc",
+           "cbp_multi_workspace_bytes", "cbp_multi_launch_info", "cbp_decode_multi", "cbp_phi",
            "cbp_strerror")
+MULTI_MAX_ITEMS = 8
 
 
 class CbpError(RuntimeError):
@@ -39,6 +41,16 @@ class CbpError(RuntimeError):
 class _Opts(C.Structure):
     _fields_ = [("alg", C.c_int), ("alpha", C.c_float), ("stop_mode", C.c_int),
                 ("soft_out", C.c_void_p)]
+
+
+class _MultiItem(C.Structure):
+    _fields_ = [("code", C.c_void_p), ("llr", C.c_void_p), ("hard_out", C.c_void_p),
+                ("iters_out", C.c_void_p), ("batch", C.c_int)]
+
+
+class _MultiOpts(C.Structure):
+    _fields_ = [("frames_per_group", C.c_int), ("chk_shared", C.c_int), ("threads", C.c_int),
+                ("ctas_per_sm", C.c_int), ("rounds_per_chunk", C.c_int), ("stop_mode", C.c_int)]
 
 
 _lock = threading.Lock()
@@ -75,6 +87,13 @@ def lib(build_if_needed: bool = True):
             L.cbp_decode_grad.argtypes = [P, P, P, I, I, I, P, P, P, P, Z, P]
             L.cbp_decode_noalloc.restype = I
             L.cbp_decode_noalloc.argtypes = [P, P, P, P, I, I, P]
+            MI, MO = C.POINTER(_MultiItem), C.POINTER(_MultiOpts)
+            L.cbp_multi_workspace_bytes.restype = I
+            L.cbp_multi_workspace_bytes.argtypes = [MI, I, MO, C.POINTER(Z)]
+            L.cbp_multi_launch_info.restype = I
+            L.cbp_multi_launch_info.argtypes = [MI, I, MO, C.POINTER(I)]
+            L.cbp_decode_multi.restype = I
+            L.cbp_decode_multi.argtypes = [MI, I, I, P, Z, P, MO]
             L.cbp_phi.restype = I
             L.cbp_phi.argtypes = [P, P, C.c_int64, P]
             L.cbp_strerror.restype = C.c_char_p
@@ -216,7 +235,7 @@ def unpack_bits(words: torch.Tensor, N: int) -> torch.Tensor:
     w = words.to(torch.int64) & 0xFFFFFFFF
     shifts = torch.arange(32, device=w.device, dtype=torch.int64)
     b = (w[:, :, None] >> shifts) & 1
-    return b.reshape(w.shape[0], -1)[:, :N].to(torch.uint8)
+    return b.reshape(w.shape[0], w.shape[1] * 32)[:, :N].to(torch.uint8)
 
 
 # ----------------------------------------------------------------------------- differentiable
@@ -266,3 +285,78 @@ def weighted_cbp(code: Code, llr: torch.Tensor, weights: torch.Tensor, T: int,
     check (all ones = plain CBP with T sweeps).  Gradients flow to ``weights`` and
     ``llr`` through the library's adjoint kernel."""
     return _WeightedCBP.apply(llr, weights, code, int(T), int(ckpt_every))
+
+
+# ----------------------------------------------------------------------------- several codes
+def multi_opts(frames_per_group: int = 0, chk_shared: int = -1, threads: int = 0,
+               ctas_per_sm: int = 0, rounds_per_chunk: int = 0,
+               stop: str = "syndrome") -> _MultiOpts:
+    """Launch options of cbp_decode_multi (0 / -1 = the library's default)."""
+    return _MultiOpts(int(frames_per_group), int(chk_shared), int(threads), int(ctas_per_sm),
+                      int(rounds_per_chunk), STOPS[stop])
+
+
+def _multi_items(codes, batches, llrs=None, hards=None, iters=None):
+    if len(codes) != len(batches):
+        raise ValueError("one batch size per code")
+    if len(codes) > MULTI_MAX_ITEMS:
+        raise ValueError(f"at most {MULTI_MAX_ITEMS} codes per launch")
+    arr = (_MultiItem * max(1, len(codes)))()
+    for i, (code, b) in enumerate(zip(codes, batches)):
+        arr[i].code = code._h.value
+        arr[i].batch = int(b)
+        if llrs is not None:
+            x, h, it = llrs[i], hards[i], iters[i]
+            if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous():
+                raise ValueError("llr tensors must be contiguous float32 CUDA tensors")
+            if x.numel() != b * code.N or h.numel() < b * code.words or it.numel() < b:
+                raise ValueError(f"item {i}: buffer sizes do not match the batch")
+            arr[i].llr, arr[i].hard_out, arr[i].iters_out = (
+                x.data_ptr(), h.data_ptr(), it.data_ptr())
+    return arr
+
+
+def multi_workspace_bytes(codes, batches, **opts) -> int:
+    """Workspace bytes of one cbp_decode_multi launch (cbp_multi_workspace_bytes)."""
+    nb = C.c_size_t()
+    o = multi_opts(**opts)
+    _check("cbp_multi_workspace_bytes",
+           lib().cbp_multi_workspace_bytes(_multi_items(codes, batches), len(codes), C.byref(o),
+                                           C.byref(nb)))
+    return nb.value
+
+
+def multi_launch_info(codes, batches, **opts) -> dict:
+    """The launch cbp_decode_multi would use (cbp_multi_launch_info)."""
+    info = (C.c_int * 8)()
+    o = multi_opts(**opts)
+    _check("cbp_multi_launch_info",
+           lib().cbp_multi_launch_info(_multi_items(codes, batches), len(codes), C.byref(o), info))
+    keys = ("ctas", "threads_per_cta", "shared_bytes", "ctas_per_sm", "chunks",
+            "check_state_shared", "frames_per_lane_group")
+    return dict(zip(keys, list(info)))
+
+
+def decode_multi_into(codes, llrs, hards, iters, max_iter: int = 30,
+                      workspace: torch.Tensor | None = None, stream=None, **opts) -> None:
+    """cbp_decode_multi on caller-provided device tensors: llrs[i] [B_i, N_i] float32,
+    hards[i] [B_i, ceil(N_i/32)] int32, iters[i] [B_i] int32."""
+    batches = [x.shape[0] for x in llrs]
+    arr = _multi_items(codes, batches, llrs, hards, iters)
+    o = multi_opts(**opts)
+    if workspace is None:
+        need = multi_workspace_bytes(codes, batches, **opts)
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=llrs[0].device)
+    _check("cbp_decode_multi",
+           lib().cbp_decode_multi(arr, len(codes), int(max_iter), workspace.data_ptr(),
+                                  workspace.numel(), _stream_ptr(stream), C.byref(o)))
+
+
+def decode_multi(codes, llrs, max_iter: int = 30, stream=None, **opts):
+    """Decode several codes' frames in one launch.  Returns [(hard, iters)] per code."""
+    hards = [torch.empty((x.shape[0], c.words), dtype=torch.int32, device=x.device)
+             for c, x in zip(codes, llrs)]
+    its = [torch.empty((x.shape[0],), dtype=torch.int32, device=x.device) for x in llrs]
+    decode_multi_into(codes, [x.contiguous() for x in llrs], hards, its, max_iter,
+                      stream=stream, **opts)
+    return list(zip(hards, its))

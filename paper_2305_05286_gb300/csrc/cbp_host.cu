@@ -53,6 +53,7 @@ struct DeviceInfo {
   bool ready = false;
   int sms = 0;
   int smem_optin = 0;
+  int smem_sm = 0;        // shared memory per SM
   float4* tab = nullptr;  // device address of g_phi_tab on this device
   float xlo = 0.0f;
 };
@@ -77,6 +78,8 @@ int device_init(int dev, DeviceInfo** out) {
     if (cudaGetSymbolAddress(&addr, g_phi_tab) != cudaSuccess) return CBP_ECUDA;
     if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&d.smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
             cudaSuccess)
       return CBP_ECUDA;
     const Variant all[] = {{ALG_CBP_SP, true, 1},  {ALG_CBP_SP, false, 1},
@@ -87,6 +90,16 @@ int device_init(int dev, DeviceInfo** out) {
     for (const Variant& v : all)
       if (decoder_set_smem(v, d.smem_optin) != cudaSuccess) return CBP_ECUDA;
     if (grad_set_smem(d.smem_optin) != cudaSuccess) return CBP_ECUDA;
+    for (int chk = 0; chk < 2; ++chk)
+      for (int fpt = 1; fpt <= 2; ++fpt) {
+        void* k = sp_multi_kernel_ptr(chk != 0, fpt);
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, k) != cudaSuccess ||
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 d.smem_optin - static_cast<int>(fa.sharedSizeBytes)) !=
+                cudaSuccess)
+          return CBP_ECUDA;
+      }
     d.tab = static_cast<float4*>(addr);
     d.xlo = xlo;
     d.ready = true;
@@ -345,6 +358,43 @@ int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan*
   return CBP_OK;
 }
 
+// Kernel parameters of one code under a plan (buffers are filled in by the caller).
+KParams code_params(const cbp_code* c, const DeviceInfo& di, const Plan& pl, int batch,
+                    int max_iter, int stop, float alpha) {
+  KParams p{};
+  p.edges = c->d.edges;
+  p.rptr = c->d.rptr;
+  p.cols = c->d.cols;
+  p.cptr = c->d.cptr;
+  p.phi_tab = di.tab;
+  p.phi_xlo = di.xlo;
+  p.Z = c->Z;
+  p.mb = c->mb;
+  p.nb = c->nb;
+  p.nnzb = c->nnzb;
+  p.N = c->N;
+  p.M = c->M;
+  p.E = c->E;
+  p.words = (c->N + 31) / 32;
+  p.batch = batch;
+  p.max_iter = max_iter;
+  p.stop = stop;
+  p.alpha = alpha;
+  p.F = pl.F;
+  p.team_groups = team_groups_for(c->Z, pl.F);
+  p.slots = pl.grid * pl.F * pl.v.fpt;
+  p.maxdeg = c->maxdeg;
+  p.ncomp = c->ncomp;
+  p.nself = c->nself;
+  p.ws_slot = pl.ws.slot;
+  p.ws_off_sv = pl.ws.off_sv;
+  p.ws_off_s = pl.ws.off_s;
+  p.ws_off_c = pl.ws.off_c;
+  p.ws_cta = static_cast<long long>(pl.F) * pl.ws.slot;
+  p.sh_frame = pl.sh_frame;
+  return p;
+}
+
 int check_opts(const cbp_opts_t* o, int* alg, float* alpha, int* stop, float** soft) {
   *alg = CBP_ALG_CBP_SP;
   *alpha = 0.75f;
@@ -563,41 +613,12 @@ int cbp_decode_ex(const cbp_code_t* c, const float* llr, uint32_t* hard_out, int
   if (int rc = make_plan(c, *di, alg, batch, &pl)) return rc;
   if (workspace_bytes < pl.ws_bytes) return CBP_EWORKSPACE;
 
-  KParams p{};
+  KParams p = code_params(c, *di, pl, batch, max_iter, stop, alpha);
   p.llr = llr;
   p.hard = hard_out;
   p.iters = iters_out;
   p.soft = soft;
   p.ws = static_cast<float*>(workspace);
-  p.edges = c->d.edges;
-  p.rptr = c->d.rptr;
-  p.cols = c->d.cols;
-  p.cptr = c->d.cptr;
-  p.phi_tab = di->tab;
-  p.phi_xlo = di->xlo;
-  p.Z = c->Z;
-  p.mb = c->mb;
-  p.nb = c->nb;
-  p.nnzb = c->nnzb;
-  p.N = c->N;
-  p.M = c->M;
-  p.E = c->E;
-  p.words = (c->N + 31) / 32;
-  p.batch = batch;
-  p.max_iter = max_iter;
-  p.stop = stop;
-  p.alpha = alpha;
-  p.F = pl.F;
-  p.team_groups = team_groups_for(c->Z, pl.F);
-  p.slots = pl.grid * pl.F * pl.v.fpt;
-  p.maxdeg = c->maxdeg;
-  p.ncomp = c->ncomp;
-  p.nself = c->nself;
-  p.ws_slot = pl.ws.slot;
-  p.ws_off_sv = pl.ws.off_sv;
-  p.ws_off_s = pl.ws.off_s;
-  p.ws_off_c = pl.ws.off_c;
-  p.sh_frame = pl.sh_frame;
   cudaError_t e = launch_decoder(pl.v, p, pl.grid, pl.threads, pl.smem,
                                  reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? CBP_OK : CBP_ECUDA;
@@ -773,44 +794,192 @@ int cbp_decode_noalloc(const cbp_code_t* c, const float* llr, uint32_t* hard_out
   pl.grid = static_cast<int>(std::min<long long>(pl.grid, max_grid));
   pl.ws_bytes = static_cast<size_t>(pl.grid) * pl.F * slot_bytes;
 
-  KParams p{};
+  KParams p = code_params(c, *di, pl, batch, max_iter, CBP_STOP_SYNDROME, 0.75f);
   p.llr = llr;
   p.hard = hard_out;
   p.iters = iters_out;
-  p.soft = nullptr;
   p.ws = static_cast<float*>(scratch);
-  p.edges = c->d.edges;
-  p.rptr = c->d.rptr;
-  p.cols = c->d.cols;
-  p.cptr = c->d.cptr;
-  p.phi_tab = di->tab;
-  p.phi_xlo = di->xlo;
-  p.Z = c->Z;
-  p.mb = c->mb;
-  p.nb = c->nb;
-  p.nnzb = c->nnzb;
-  p.N = c->N;
-  p.M = c->M;
-  p.E = c->E;
-  p.words = (c->N + 31) / 32;
-  p.batch = batch;
-  p.max_iter = max_iter;
-  p.stop = CBP_STOP_SYNDROME;
-  p.alpha = 0.75f;
-  p.F = pl.F;
-  p.team_groups = team_groups_for(c->Z, pl.F);
-  p.slots = pl.grid * pl.F * pl.v.fpt;
-  p.maxdeg = c->maxdeg;
-  p.ncomp = c->ncomp;
-  p.nself = c->nself;
-  p.ws_slot = pl.ws.slot;
-  p.ws_off_sv = pl.ws.off_sv;
-  p.ws_off_s = pl.ws.off_s;
-  p.ws_off_c = pl.ws.off_c;
-  p.sh_frame = pl.sh_frame;
   cudaError_t e = launch_decoder(pl.v, p, pl.grid, pl.threads, pl.smem,
                                  reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? CBP_OK : CBP_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Several codes in one persistent launch (CBP-SP).
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+struct MultiPlan {
+  MultiParams mp{};
+  int grid = 0, threads = 0, ctas_per_sm = 0, chunks = 0, fpt = 1;
+  bool chk = false;
+  size_t smem = 0, ws_bytes = 0;
+};
+
+constexpr size_t kCounterBytes = 256;  // work counter at the start of the workspace
+
+// Lane groups, shared memory and workspace of every item under one CTA shape; items
+// ordered heaviest chunk first (a chunk's time grows with the code's base entries and
+// with the frame rounds it holds).
+int multi_plan_try(const cbp_multi_item_t* items, int n, int max_iter, int stop, bool chk,
+                   int fpt, int threads, int ctas_target, int rounds, MultiPlan* out) {
+  DeviceInfo* di = nullptr;
+  int dev = 0;
+  if (int rc = current_device(&di, &dev)) return rc;
+  void* kern = sp_multi_kernel_ptr(chk, fpt);
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return CBP_ECUDA;
+  if (threads > fa.maxThreadsPerBlock) return CBP_EINVAL;
+  const long long budget_sm = di->smem_sm / ctas_target - 1024 - static_cast<long long>(fa.sharedSizeBytes);
+  const long long budget = std::min<long long>(budget_sm, di->smem_optin - static_cast<long long>(fa.sharedSizeBytes));
+  MultiPlan pl;
+  pl.threads = threads;
+  pl.fpt = fpt;
+  pl.chk = chk;
+  const Variant v{ALG_CBP_SP, chk, fpt};
+  std::vector<int> order;
+  std::vector<KParams> kp(n);
+  std::vector<int> cf(n, 0);
+  long long ws_cta = 0;
+  for (int i = 0; i < n; ++i) {
+    const cbp_code* c = items[i].code;
+    if (c->dev != dev) return CBP_EDEVICE;
+    if (c->Z > threads) return CBP_EUNSUPPORTED;
+    if (items[i].batch == 0) continue;
+    const Shape sh = c->shape();
+    const size_t fr = shared_frame_floats(v, sh);
+    int G = 0;
+    size_t smem = 0;
+    for (int g = 1; g * c->Z <= threads; ++g) {
+      const size_t b = shared_fixed_bytes(v, sh, g) + g * fr * sizeof(float);
+      if (static_cast<long long>(b) > budget) break;
+      G = g;
+      smem = b;
+    }
+    if (G == 0) return CBP_EUNSUPPORTED;
+    Plan cp;
+    cp.v = v;
+    cp.F = G;
+    cp.grid = 0;
+    cp.ws = ws_layout(v, sh);
+    cp.sh_frame = static_cast<int>(fr);
+    kp[i] = code_params(c, *di, cp, items[i].batch, max_iter, stop, 0.75f);
+    kp[i].llr = items[i].llr;
+    kp[i].hard = items[i].hard_out;
+    kp[i].iters = items[i].iters_out;
+    cf[i] = G * fpt * rounds;
+    pl.smem = std::max(pl.smem, smem);
+    ws_cta = std::max<long long>(ws_cta, static_cast<long long>(G) * cp.ws.slot);
+    order.push_back(i);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return 1LL * items[a].code->nnzb * rounds > 1LL * items[b].code->nnzb * rounds;
+  });
+  pl.mp.ncodes = static_cast<int>(order.size());
+  long long chunks = 0;
+  for (size_t j = 0; j < order.size(); ++j) {
+    const int i = order[j];
+    kp[i].ws_cta = ws_cta;
+    pl.mp.code[j] = kp[i];
+    pl.mp.chunk_frames[j] = cf[i];
+    chunks += (items[i].batch + cf[i] - 1) / cf[i];
+    if (chunks > (1LL << 30)) return CBP_EUNSUPPORTED;
+    pl.mp.chunk_end[j] = static_cast<int>(chunks);
+  }
+  pl.chunks = static_cast<int>(chunks);
+  int ctas = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, kern, threads, pl.smem) != cudaSuccess)
+    return CBP_ECUDA;
+  if (ctas < 1) return CBP_EUNSUPPORTED;
+  pl.ctas_per_sm = ctas;
+  pl.grid = static_cast<int>(std::max(1LL, std::min<long long>(chunks, 1LL * di->sms * ctas)));
+  pl.ws_bytes = kCounterBytes + static_cast<size_t>(pl.grid) * ws_cta * sizeof(float);
+  *out = pl;
+  return CBP_OK;
+}
+
+int multi_plan(const cbp_multi_item_t* items, int n, const cbp_multi_opts_t* o, int max_iter,
+               MultiPlan* out) {
+  if (n < 0 || (n > 0 && !items)) return CBP_EINVAL;
+  if (n > CBP_MULTI_MAX_ITEMS) return CBP_EINVAL;
+  cbp_multi_opts_t d{};
+  d.chk_shared = -1;
+  if (o) d = *o;
+  const int fpt = d.frames_per_group == 0 ? 1 : d.frames_per_group;
+  if (fpt != 1 && fpt != 2) return CBP_EINVAL;
+  const int tmax = fpt == 2 ? 384 : 768;
+  const int threads = d.threads == 0 ? tmax : d.threads;
+  if (threads < 32 || threads > tmax || threads % 32) return CBP_EINVAL;
+  const int ctas = d.ctas_per_sm == 0 ? 1 : d.ctas_per_sm;
+  const int rounds = d.rounds_per_chunk == 0 ? 4 : d.rounds_per_chunk;
+  if (ctas < 1 || ctas > 32 || rounds < 1 || rounds > 4096) return CBP_EINVAL;
+  if (d.stop_mode != CBP_STOP_SYNDROME && d.stop_mode != CBP_STOP_NONE) return CBP_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!items[i].code || items[i].batch < 0) return CBP_EINVAL;
+  if (d.chk_shared == 0 || d.chk_shared == 1)
+    return multi_plan_try(items, n, max_iter, d.stop_mode, d.chk_shared == 1, fpt, threads, ctas,
+                          rounds, out);
+  const int rc = multi_plan_try(items, n, max_iter, d.stop_mode, true, fpt, threads, ctas, rounds,
+                                out);
+  if (rc != CBP_EUNSUPPORTED) return rc;
+  return multi_plan_try(items, n, max_iter, d.stop_mode, false, fpt, threads, ctas, rounds, out);
+}
+
+}  // namespace
+
+extern "C" {
+
+int cbp_multi_workspace_bytes(const cbp_multi_item_t* items, int n_items,
+                              const cbp_multi_opts_t* opts, size_t* bytes) {
+  if (!bytes) return CBP_EINVAL;
+  MultiPlan pl;
+  if (int rc = multi_plan(items, n_items, opts, 1, &pl)) return rc;
+  *bytes = pl.mp.ncodes == 0 ? 0 : pl.ws_bytes;
+  return CBP_OK;
+}
+
+int cbp_multi_launch_info(const cbp_multi_item_t* items, int n_items,
+                          const cbp_multi_opts_t* opts, int* info) {
+  if (!info) return CBP_EINVAL;
+  MultiPlan pl;
+  if (int rc = multi_plan(items, n_items, opts, 1, &pl)) return rc;
+  info[0] = pl.mp.ncodes == 0 ? 0 : pl.grid;
+  info[1] = pl.threads;
+  info[2] = static_cast<int>(pl.smem);
+  info[3] = pl.ctas_per_sm;
+  info[4] = pl.chunks;
+  info[5] = pl.chk ? 1 : 0;
+  info[6] = pl.fpt;
+  info[7] = 0;
+  return CBP_OK;
+}
+
+int cbp_decode_multi(const cbp_multi_item_t* items, int n_items, int max_iter, void* workspace,
+                     size_t workspace_bytes, cbp_stream_t stream, const cbp_multi_opts_t* opts) {
+  if (max_iter < 1) return CBP_EINVAL;
+  for (int i = 0; i < n_items && items; ++i) {
+    const cbp_multi_item_t& it = items[i];
+    if (it.batch <= 0) continue;
+    if (!it.llr || !it.hard_out || !it.iters_out) return CBP_EINVAL;
+    if (!aligned(it.llr, 16) || !aligned(it.hard_out, 4) || !aligned(it.iters_out, 4))
+      return CBP_EINVAL;
+  }
+  MultiPlan pl;
+  if (int rc = multi_plan(items, n_items, opts, max_iter, &pl)) return rc;
+  if (pl.mp.ncodes == 0) return CBP_OK;
+  if (!workspace || !aligned(workspace, 256)) return CBP_EINVAL;
+  if (workspace_bytes < pl.ws_bytes) return CBP_EWORKSPACE;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  pl.mp.counter = reinterpret_cast<int*>(ws);
+  for (int j = 0; j < pl.mp.ncodes; ++j)
+    pl.mp.code[j].ws = reinterpret_cast<float*>(ws + kCounterBytes);
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(pl.mp.counter, 0, sizeof(int), st) != cudaSuccess) return CBP_ECUDA;
+  return launch_multi(pl.chk, pl.fpt, pl.mp, pl.grid, pl.threads, pl.smem, st) == cudaSuccess
+             ? CBP_OK
+             : CBP_ECUDA;
 }
 
 int cbp_phi(const float* x, float* y, int64_t n, cbp_stream_t stream) {

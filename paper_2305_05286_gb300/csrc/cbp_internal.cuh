@@ -117,10 +117,21 @@ struct KParams {
   int maxdeg;
   int ncomp, nself;      // columns of weight >= 2 / of weight 1
   long long ws_slot;     // floats of workspace per lane group
+  long long ws_cta;      // CBP-SP: floats of workspace per CTA (>= F * ws_slot)
   long long ws_off_sv;   // offset (floats) of the weight-1 column state
   long long ws_off_s;    // CBP-SP: check-beliefs when not shared; min-sum: check state
   long long ws_off_c;    // CBP min-sum: (min1, min2) per check when not shared
   int sh_frame;          // floats of shared memory per lane group
+};
+
+// Several codes in one launch (CBP-SP): per-code parameters and the chunk list.
+constexpr int kMaxMultiCodes = 8;
+struct MultiParams {
+  KParams code[kMaxMultiCodes];
+  int chunk_end[kMaxMultiCodes];     // exclusive prefix end of each code's chunks
+  int chunk_frames[kMaxMultiCodes];  // frames per chunk of each code
+  int* counter;                      // next chunk (zeroed before the launch)
+  int ncodes;
 };
 
 enum Alg { ALG_CBP_SP = 0, ALG_CBP_NMS = 1, ALG_LBP_NMS = 2, ALG_FBP_SP = 3 };
@@ -151,6 +162,9 @@ cudaError_t decoder_func_attrs(const Variant& v, cudaFuncAttributes* a);
 cudaError_t decoder_set_smem(const Variant& v, int bytes);
 cudaError_t decoder_occupancy(const Variant& v, int threads, size_t smem, int* ctas);
 void* sp_kernel_ptr(bool chk_shared, int fpt, bool wide);  // cbp_sp.cu
+void* sp_multi_kernel_ptr(bool chk_shared, int fpt);        // cbp_sp.cu
+cudaError_t launch_multi(bool chk_shared, int fpt, const MultiParams& mp, int grid, int threads,
+                         size_t smem, cudaStream_t st);
 void* minsum_kernel_ptr(int alg, bool chk_shared);          // cbp_minsum.cu
 void* flood_kernel_ptr();              // cbp_flood.cu
 cudaError_t launch_phi(const float* x, float* y, long long n, const float4* tab, float xlo,

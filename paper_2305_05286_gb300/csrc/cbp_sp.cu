@@ -125,10 +125,13 @@ __device__ __forceinline__ void update_chunk(const Chunk<FPT, CH>& c, int kb, in
   }
 }
 
-template <bool CHKS, int FPT, int CH, bool DB, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) cbp_sp_kernel(const KParams p) {
+// Decode frames frame0, frame0 + 1, ... of one code with the lane groups of this CTA:
+// frame slot k starts at frame0 + k and advances by `stride` when its frame stops, until
+// it passes `end`.  Returns when every slot of the CTA is idle.
+template <bool CHKS, int FPT, int CH, bool DB>
+__device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride, int end,
+                                        unsigned char* smem, bool load_tab) {
   using LV = Lanes<FPT>;
-  extern __shared__ __align__(16) unsigned char smem[];
   const int Z = p.Z, N = p.N, M = p.M, words = p.words, G = p.F;
   const int tid = threadIdx.x;
   const int g = tid / Z;
@@ -148,7 +151,8 @@ __global__ void __launch_bounds__(MAXT, 1) cbp_sp_kernel(const KParams p) {
   sp += sizeof(SlotState) * ((G * FPT + 3) & ~3);
   float* s_groups = reinterpret_cast<float*>(sp);
 
-  for (int i = tid; i < kPhiSegments; i += blockDim.x) s_tab[i] = p.phi_tab[i];
+  if (load_tab)
+    for (int i = tid; i < kPhiSegments; i += blockDim.x) s_tab[i] = p.phi_tab[i];
   for (int i = tid; i < p.nnzb; i += blockDim.x) s_e[i] = p.edges[i];
   for (int i = tid; i <= p.mb; i += blockDim.x) s_rptr[i] = p.rptr[i];
   for (int c = tid; c < p.nb; c += blockDim.x) {
@@ -158,7 +162,7 @@ __global__ void __launch_bounds__(MAXT, 1) cbp_sp_kernel(const KParams p) {
                           (be.pad & 0xffffu) | ((be.flags & kSelf) ? 0x10000u : 0u));
   }
   for (int k = tid; k < G * FPT; k += blockDim.x) {
-    s_slot[k].frame = blockIdx.x * G * FPT + k;
+    s_slot[k].frame = frame0 + k;
     s_slot[k].t = 0;
     s_slot[k].unsat = 0;
   }
@@ -166,8 +170,9 @@ __global__ void __launch_bounds__(MAXT, 1) cbp_sp_kernel(const KParams p) {
   float* gbase = s_groups + static_cast<size_t>(lane ? g : 0) * p.sh_frame;
   float* QP = gbase;
   float* nxt = gbase + 2 * FPT * static_cast<size_t>(p.ncomp) * Z;
-  const long long gslot = static_cast<long long>(blockIdx.x) * G + (lane ? g : 0);
-  float* wsl = p.ws + gslot * p.ws_slot;
+  // this CTA's workspace region, then the lane group's part of it
+  float* wsl = p.ws + static_cast<long long>(blockIdx.x) * p.ws_cta +
+               static_cast<long long>(lane ? g : 0) * p.ws_slot;
   float* R = wsl;                       // [E][FPT]
   float* SV = wsl + p.ws_off_sv;        // [nself*Z][FPT](Q,phi)
   float* S;
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(MAXT, 1) cbp_sp_kernel(const KParams p) {
   const float xlo = p.phi_xlo;
   // teams of p.team_groups lane groups (whole warps) synchronise among themselves
   const int tg = p.team_groups;
-  const bool single_team = tg >= G;
+  const bool single_team = tg >= G || G * Z != static_cast<int>(blockDim.x);
   const int bar_id = single_team ? 0 : 1 + (lane ? g / tg : 0);
   const int bar_n = single_team ? static_cast<int>(blockDim.x) : tg * Z;
   __syncthreads();
@@ -195,8 +200,8 @@ __global__ void __launch_bounds__(MAXT, 1) cbp_sp_kernel(const KParams p) {
     bool any = false;
 #pragma unroll
     for (int h = 0; h < FPT; ++h) {
-      frame[h] = lane ? my[h].frame : p.batch;
-      act[h] = frame[h] < p.batch;
+      frame[h] = lane ? my[h].frame : end;
+      act[h] = frame[h] < end;
       any |= act[h];
       if (act[h] && my[h].t == 0) {  // Step 1, Eq. (s4e15): Q*_v = L_v for frame h
         const float* src = p.llr + static_cast<long long>(frame[h]) * N;
@@ -351,7 +356,7 @@ __global__ void __launch_bounds__(MAXT, 1) cbp_sp_kernel(const KParams p) {
       for (int h = 0; h < FPT; ++h)
         if (act[h]) {
           if (done[h]) {
-            my[h].frame = frame[h] + p.slots;
+            my[h].frame = frame[h] + stride;
             my[h].t = 0;
           } else {
             my[h].t = t[h];
@@ -362,7 +367,49 @@ __global__ void __launch_bounds__(MAXT, 1) cbp_sp_kernel(const KParams p) {
   }
 }
 
+template <bool CHKS, int FPT, int CH, bool DB, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) cbp_sp_kernel(const KParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  sp_body<CHKS, FPT, CH, DB>(p, blockIdx.x * p.F * FPT, p.slots, p.batch, smem, true);
+}
+
+// Several codes in one persistent launch: each CTA takes chunks (code, frame range) from
+// a work counter and decodes them with that code's lane-group layout.
+template <bool CHKS, int FPT, int CH, bool DB, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) cbp_sp_multi_kernel(const MultiParams mp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  // the chunk's code parameters live in shared memory (read like kernel parameters)
+  __shared__ KParams s_p;
+  __shared__ int s_chunk[2];  // chunk index, frame range start
+  const int total = mp.chunk_end[mp.ncodes - 1];
+  for (bool first_chunk = true;; first_chunk = false) {
+    if (threadIdx.x == 0) {
+      const int c = atomicAdd(mp.counter, 1);
+      s_chunk[0] = c;
+      if (c < total) {
+        int k = 0;
+        while (c >= mp.chunk_end[k]) ++k;
+        s_p = mp.code[k];
+        s_chunk[1] = (k == 0 ? c : c - mp.chunk_end[k - 1]) * mp.chunk_frames[k];
+        s_p.batch = min(s_chunk[1] + mp.chunk_frames[k], s_p.batch);  // range end
+      }
+    }
+    __syncthreads();
+    if (s_chunk[0] >= total) break;
+    sp_body<CHKS, FPT, CH, DB>(s_p, s_chunk[1], s_p.F * FPT, s_p.batch, smem, first_chunk);
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+void* sp_multi_kernel_ptr(bool chk_shared, int fpt) {
+  if (fpt == 2)
+    return chk_shared ? reinterpret_cast<void*>(&cbp_sp_multi_kernel<true, 2, 4, true, 384>)
+                      : reinterpret_cast<void*>(&cbp_sp_multi_kernel<false, 2, 4, true, 384>);
+  return chk_shared ? reinterpret_cast<void*>(&cbp_sp_multi_kernel<true, 1, 4, false, 768>)
+                    : reinterpret_cast<void*>(&cbp_sp_multi_kernel<false, 1, 4, false, 768>);
+}
 
 void* sp_kernel_ptr(bool chk_shared, int fpt, bool wide) {
   // wide: up to 1024 threads per CTA (Z > 512), fewer registers per thread

@@ -1,0 +1,71 @@
+"""Launch autotuner for the several-codes decoder (cbp_decode_multi).
+
+The library's default launch shape (one 768-thread CTA per SM, four frame rounds per
+chunk) is a safe choice, not always the fastest: small lifting sizes leave lanes
+idle, two interleaved frames per lane group hide more latency, and smaller chunks
+balance better when few frames are left.  `tune_multi` times each candidate option
+set on the caller's own frames with CUDA events and returns the fastest.  All
+decoding runs in libcbp; this module only chooses among its launch options.
+"""
+from __future__ import annotations
+
+import itertools
+
+import torch
+
+from . import cbp
+
+
+def candidates(codes, fpts=(1, 2), chks=(1, 0), ctas=(1, 2), rounds=(1, 2, 4, 8)):
+    """Option sets worth timing: every combination whose CTA can hold each code's
+    lifting size (threads >= Z) and that the library can plan."""
+    zmax = max(c.Z for c in codes)
+    out = []
+    for fpt, chk, cps, r in itertools.product(fpts, chks, ctas, rounds):
+        tmax = 384 if fpt == 2 else 768
+        threads = tmax // cps if cps > 1 and tmax // cps >= zmax else tmax
+        if threads < zmax:
+            continue
+        out.append(dict(frames_per_group=fpt, chk_shared=chk, threads=threads,
+                        ctas_per_sm=cps, rounds_per_chunk=r))
+    return out
+
+
+def time_multi(codes, llrs, opts: dict, max_iter: int = 30, reps: int = 3,
+               warmup: int = 1) -> float:
+    """Mean milliseconds of one cbp_decode_multi launch with `opts` on these frames."""
+    batches = [x.shape[0] for x in llrs]
+    need = cbp.multi_workspace_bytes(codes, batches, **opts)
+    ws = torch.empty(max(need, 256), dtype=torch.uint8, device=llrs[0].device)
+    hards = [torch.empty((b, c.words), dtype=torch.int32, device=ws.device)
+             for c, b in zip(codes, batches)]
+    its = [torch.empty((b,), dtype=torch.int32, device=ws.device) for b in batches]
+    for _ in range(warmup):
+        cbp.decode_multi_into(codes, llrs, hards, its, max_iter, ws, **opts)
+    st = torch.cuda.current_stream()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(st)
+    for _ in range(reps):
+        cbp.decode_multi_into(codes, llrs, hards, its, max_iter, ws, **opts)
+    t1.record(st)
+    t1.synchronize()
+    return t0.elapsed_time(t1) / reps
+
+
+def tune_multi(codes, llrs, max_iter: int = 30, reps: int = 3, cands=None):
+    """Time every candidate; returns (best options, [(ms, options)] sorted fastest first).
+    Candidates the library rejects for these codes (CBP_EUNSUPPORTED) are skipped."""
+    table = []
+    for o in cands if cands is not None else candidates(codes):
+        try:
+            ms = time_multi(codes, llrs, o, max_iter, reps)
+        except cbp.CbpError as e:
+            if e.status == -4:
+                continue
+            raise
+        table.append((ms, o))
+    if not table:
+        raise RuntimeError("no launch option set fits these codes")
+    table.sort(key=lambda t: t[0])
+    return table[0][1], table
