@@ -43,6 +43,26 @@ void phi_table_host(float* coef, float* xlo) {
   *xlo = static_cast<float>(std::log1p(2.0 / std::expm1(30.0)));
 }
 
+// Coefficient k divided by h^k: h = 2^(e - 1) for a centre m = f 2^e (f in [0.5, 1)),
+// h = 1/16 above 2.  ldexp by a power of two is exact while the value stays normal,
+// which every coefficient does (the largest, |c3| / h^3 at m = 2^-43, is about 2^127.4).
+void phi_table_device_form(const float* coef, float* dev) {
+  for (int i = 0; i < kPhiSegments; ++i) {
+    int lh;  // log2 h
+    if (i < kPhiLogCount) {
+      uint32_t u = static_cast<uint32_t>(kPhiLogBase + i) << 18;
+      float mf;
+      std::memcpy(&mf, &u, sizeof mf);
+      int ex;
+      std::frexp(static_cast<double>(mf), &ex);
+      lh = ex - 1;
+    } else {
+      lh = -4;
+    }
+    for (int k = 0; k < 4; ++k) dev[4 * i + k] = std::ldexp(coef[4 * i + k], -k * lh);
+  }
+}
+
 __device__ float4 g_phi_tab[kPhiSegments];
 
 namespace {
@@ -69,8 +89,10 @@ int device_init(int dev, DeviceInfo** out) {
     static std::vector<float> coef;
     static float xlo = 0.0f;
     if (coef.empty()) {
+      std::vector<float> t_form(4 * kPhiSegments);
+      phi_table_host(t_form.data(), &xlo);
       coef.resize(4 * kPhiSegments);
-      phi_table_host(coef.data(), &xlo);
+      phi_table_device_form(t_form.data(), coef.data());
     }
     if (cudaMemcpyToSymbol(g_phi_tab, coef.data(), sizeof(float) * coef.size()) != cudaSuccess)
       return CBP_ECUDA;
@@ -126,8 +148,9 @@ size_t shared_fixed_bytes(const Variant& v, const Shape& s, int groups) {
   size_t b = sizeof(BaseEdge) * s.nnzb + sizeof(int) * align4(s.mb + 1) +
              12 * align4(static_cast<size_t>(groups) * v.fpt);
   switch (v.alg) {
-    case ALG_CBP_SP:
+    case ALG_CBP_SP:  // SpEdge records in place of the BaseEdge list (same size)
       b += sizeof(float4) * kPhiSegments + sizeof(uint2) * ((s.nb + 1) & ~1);
+      static_assert(sizeof(SpEdge) == sizeof(BaseEdge), "CBP-SP edge record size");
       break;
     case ALG_FBP_SP:
       b += sizeof(float4) * kPhiSegments + sizeof(ColEntry) * ((s.nnzb + 1) & ~1) +
@@ -363,6 +386,7 @@ KParams code_params(const cbp_code* c, const DeviceInfo& di, const Plan& pl, int
                     int max_iter, int stop, float alpha) {
   KParams p{};
   p.edges = c->d.edges;
+  p.spe = c->d.spe;
   p.rptr = c->d.rptr;
   p.cols = c->d.cols;
   p.cptr = c->d.cptr;
@@ -507,7 +531,20 @@ int cbp_code_create(const int32_t* base, int mb, int nb, int Z, cbp_code_t** out
   if (tri) c->K = c->N - c->M;
   else if (1LL * c->M * c->N <= (1LL << 24)) c->K = c->N - gf2_rank(base, mb, nb, Z);
 
+  std::vector<SpEdge> spe(edges.size());
+  for (size_t k = 0; k < edges.size(); ++k) {
+    const BaseEdge& e = edges[k];
+    const bool self = e.flags & kSelf;
+    const uint32_t sq = self ? 0u : e.s;
+    const uint32_t d = (static_cast<uint32_t>(e.s) + Z - e.ps) % static_cast<uint32_t>(Z);
+    spe[k].x = ((e.pad & 0xffffu) * static_cast<uint32_t>(Z) + sq) |
+               ((e.flags & kFirst) ? kSpFirst : 0u) | (self ? kSpSelf : 0u);
+    spe[k].y = static_cast<uint32_t>(e.pr) * Z + d;
+    spe[k].z = static_cast<uint32_t>(e.pe) * Z + d;
+    spe[k].w = (static_cast<uint32_t>(Z) - sq) | ((static_cast<uint32_t>(Z) - d) << 16);
+  }
   bool ok = cudaMalloc(&c->d.edges, sizeof(BaseEdge) * edges.size()) == cudaSuccess &&
+            cudaMalloc(&c->d.spe, sizeof(SpEdge) * spe.size()) == cudaSuccess &&
             cudaMalloc(&c->d.rptr, sizeof(int) * rptr.size()) == cudaSuccess &&
             cudaMalloc(&c->d.cols, sizeof(ColEntry) * cols.size()) == cudaSuccess &&
             cudaMalloc(&c->d.cptr, sizeof(int) * cptr.size()) == cudaSuccess;
@@ -517,6 +554,8 @@ int cbp_code_create(const int32_t* base, int mb, int nb, int Z, cbp_code_t** out
   }
   ok = cudaMemcpy(c->d.edges, edges.data(), sizeof(BaseEdge) * edges.size(),
                   cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(c->d.spe, spe.data(), sizeof(SpEdge) * spe.size(), cudaMemcpyHostToDevice) ==
+           cudaSuccess &&
        cudaMemcpy(c->d.rptr, rptr.data(), sizeof(int) * rptr.size(), cudaMemcpyHostToDevice) ==
            cudaSuccess &&
        cudaMemcpy(c->d.cols, cols.data(), sizeof(ColEntry) * cols.size(),
@@ -534,6 +573,7 @@ int cbp_code_create(const int32_t* base, int mb, int nb, int Z, cbp_code_t** out
 void cbp_code_destroy(cbp_code_t* c) {
   if (!c) return;
   cudaFree(c->d.edges);
+  cudaFree(c->d.spe);
   cudaFree(c->d.rptr);
   cudaFree(c->d.cols);
   cudaFree(c->d.cptr);

@@ -15,55 +15,60 @@ namespace cbp {
 // phi(clamp(x, X_LO, 30)) with X_LO = fl32(phi(30)); cubic Taylor polynomial around
 // the nearest grid centre: below 2 the FP32 values whose low 18 mantissa bits are
 // zero (bit patterns (2688 + i) << 18, i = 0..1408, i.e. 2^-43 .. 2.0), local variable
-// t = (x - centre) / 2^e(centre); from 2 to 30 the centres k/16, t = 16x - k.
+// t = (x - centre) / h with h = 2^e(centre); from 2 to 30 the centres k/16, h = 1/16.
+// The coefficients are phi^(k)(m) h^k / k! rounded to FP32.  The device table holds
+// them divided by h^k (exact: h is a power of two and no value leaves the normal FP32
+// range), so the kernels evaluate the same Horner steps on d = x - centre (exact by
+// Sterbenz) without forming t; every rounding is the scaled one times a power of two,
+// so the result is bit-identical to the t form.
 // ----------------------------------------------------------------------------
 constexpr int kPhiLogBase = 2688;
 constexpr int kPhiLogCount = 1409;
 constexpr int kPhiSegments = kPhiLogCount + 449;
 
-// Host: fill the coefficient table (4 floats per centre) and the lower clamp.
+// Host: fill the coefficient table (4 floats per centre, the t form) and the lower clamp.
 void phi_table_host(float* coef, float* xlo);
+// Host: the device form of the table (coefficient k divided by h^k).
+void phi_table_device_form(const float* coef, float* dev);
 
 __device__ __forceinline__ float phi_eval(float x, float xlo, const float4* __restrict__ tab) {
   x = fminf(fmaxf(x, xlo), 30.0f);
-  // below 2: nearest centre cb, t = (x - cb) * 2^-e(cb), 2^-e from the exponent field
+  // below 2: nearest centre cb (round the low 18 mantissa bits), d = x - cb
   const uint32_t cb = (__float_as_uint(x) + 0x20000u) & 0xFFFC0000u;
-  const float tl = __fmul_rn(__fsub_rn(x, __uint_as_float(cb)),
-                             __uint_as_float(0x7F000000u - (cb & 0x7F800000u)));
-  // 2 to 30: k = rint(16x) by adding 1.5 * 2^23 (16x is exact and below 2^22), t = 16x - k
+  const float dl = __fsub_rn(x, __uint_as_float(cb));
+  // 2 to 30: k = rint(16x) by adding 1.5 * 2^23 (16x is exact and below 2^22), d = x - k/16
   constexpr float kMagic = 12582912.0f;
   const float y = __fmaf_rn(x, 16.0f, kMagic);
-  const float tu = __fmaf_rn(x, 16.0f, -__fsub_rn(y, kMagic));
+  const float du = __fmaf_rn(__fsub_rn(y, kMagic), -0.0625f, x);
   const bool lo = x < 2.0f;
-  const float t = lo ? tl : tu;
+  const float d = lo ? dl : du;
   const int i = lo ? static_cast<int>(cb >> 18) - kPhiLogBase
                    : static_cast<int>(__float_as_uint(y) - __float_as_uint(kMagic)) +
                          (kPhiLogCount - 32);
   const float4 c = tab[i];
-  float p = __fmaf_rn(c.w, t, c.z);
-  p = __fmaf_rn(p, t, c.y);
-  return __fmaf_rn(p, t, c.x);
+  float p = __fmaf_rn(c.w, d, c.z);
+  p = __fmaf_rn(p, d, c.y);
+  return __fmaf_rn(p, d, c.x);
 }
 
-// Derivative of phi_eval: the derivative of the cubic of the centre's segment,
-// c1 + t (2 c2 + 3 c3 t), times dt/dx (2^-e below 2, 16 above); 0 where the clamp holds.
+// Derivative of phi_eval: the derivative of the centre's cubic, c1 + d (2 c2 + 3 c3 d),
+// on the device form of the table; 0 where the clamp holds.
 __device__ __forceinline__ float phi_deriv(float x, float xlo, const float4* __restrict__ tab) {
   const bool inside = x >= xlo && x <= 30.0f;
   x = fminf(fmaxf(x, xlo), 30.0f);
   const uint32_t cb = (__float_as_uint(x) + 0x20000u) & 0xFFFC0000u;
-  const float inv = __uint_as_float(0x7F000000u - (cb & 0x7F800000u));
-  const float tl = __fmul_rn(__fsub_rn(x, __uint_as_float(cb)), inv);
+  const float dl = __fsub_rn(x, __uint_as_float(cb));
   constexpr float kMagic = 12582912.0f;
   const float y = __fmaf_rn(x, 16.0f, kMagic);
-  const float tu = __fmaf_rn(x, 16.0f, -__fsub_rn(y, kMagic));
+  const float du = __fmaf_rn(__fsub_rn(y, kMagic), -0.0625f, x);
   const bool lo = x < 2.0f;
-  const float t = lo ? tl : tu;
+  const float d = lo ? dl : du;
   const int i = lo ? static_cast<int>(cb >> 18) - kPhiLogBase
                    : static_cast<int>(__float_as_uint(y) - __float_as_uint(kMagic)) +
                          (kPhiLogCount - 32);
   const float4 c = tab[i];
-  const float dp = __fmaf_rn(__fmaf_rn(3.0f * c.w, t, 2.0f * c.z), t, c.y);
-  return inside ? dp * (lo ? inv : 16.0f) : 0.0f;
+  const float dp = __fmaf_rn(__fmaf_rn(3.0f * c.w, d, 2.0f * c.z), d, c.y);
+  return inside ? dp : 0.0f;
 }
 
 // ----------------------------------------------------------------------------
@@ -88,8 +93,20 @@ struct ColEntry {
   uint16_t r, s, e, pad;
 };
 
+// The CBP-SP kernel's view of a base entry (row r, column c, shift s) for lane z, with
+// lane-independent parts precomputed (Z is fixed per code).  With s' = 0 for a weight-1
+// column (its state is indexed by the check lane) and s' = s otherwise, and
+// d = (s - ps) mod Z for the predecessor entry (pr, ps, pe):
+//   x = A | first << 30 | weight1 << 31, A = idx * Z + s'  (idx: compact column index)
+//   y = pr * Z + d,  z = pe * Z + d,  w = (Z - s') | (Z - d) << 16
+// so that, with u(T) = (z >= T ? Z : 0):  variable slot = A + z - u(Z - s'),
+// predecessor check = y + z - u(Z - d),  predecessor R slot = z + z - u(Z - d).
+using SpEdge = uint4;
+constexpr uint32_t kSpFirst = 1u << 30, kSpSelf = 1u << 31, kSpMask = kSpFirst - 1;
+
 struct CodeDev {
   BaseEdge* edges = nullptr;  // [nnzb]
+  SpEdge* spe = nullptr;      // [nnzb], CBP-SP kernel records
   int* rptr = nullptr;        // [mb + 1]
   ColEntry* cols = nullptr;   // [nnzb], column-major
   int* cptr = nullptr;        // [nb + 1]
@@ -103,6 +120,7 @@ struct KParams {
   float* soft;
   float* ws;
   const BaseEdge* edges;
+  const SpEdge* spe;
   const int* rptr;
   const ColEntry* cols;
   const int* cptr;

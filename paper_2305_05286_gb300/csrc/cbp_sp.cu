@@ -61,10 +61,10 @@ struct Chunk {
 };
 
 // Loads of a chunk: (Q*, phi) of each variable, S of its predecessor check c_j, and
-// the edge's own R slot (not read in a frame's first sweep).
+// the edge's own R slot (read only once the frame is past its first sweep).
 template <int FPT, int CH>
 __device__ __forceinline__ void load_chunk(Chunk<FPT, CH>& c, int kb, int k1,
-                                           const BaseEdge* __restrict__ s_e, int z, int Z,
+                                           const SpEdge* __restrict__ s_spe, int z, int Z,
                                            bool later, const float* QP, const float* SV,
                                            const float* S, const float* R) {
   using LV = Lanes<FPT>;
@@ -72,23 +72,27 @@ __device__ __forceinline__ void load_chunk(Chunk<FPT, CH>& c, int kb, int k1,
   for (int j = 0; j < CH; ++j) {
     const int k = kb + j;
     if (k < k1) {
-      const BaseEdge be = s_e[k];
-      const int zv = mod_add(z + be.s, Z);
-      const int idx = be.pad & 0xffff;
-      const bool self = be.flags & kSelf;
-      int zj = zv - be.ps;
-      zj = zj < 0 ? zj + Z : zj;
-      c.fl[j] = be.flags;
-      c.qoff[j] = self ? idx * Z + z : idx * Z + zv;
-      c.roff[j] = be.pe * Z + zj;
-      LV::ld_pair(self ? SV : QP, c.qoff[j], c.q[j], c.ph[j]);
-      LV::ld(S, be.pr * Z + zj, c.sj[j]);
-      if (later && !self) LV::ld(R, k * Z + z, c.ro[j]);
+      const SpEdge se = s_spe[k];
+      const int tq = static_cast<int>(se.w & 0xffffu), tj = static_cast<int>(se.w >> 16);
+      const int uj = z >= tj ? Z : 0;
+      c.fl[j] = se.x;
+      c.qoff[j] = static_cast<int>(se.x & kSpMask) + z - (z >= tq ? Z : 0);
+      c.roff[j] = static_cast<int>(se.z) + z - uj;
+      if (se.x & kSpSelf) {
+        LV::ld_pair(SV, c.qoff[j], c.q[j], c.ph[j]);
+      } else {
+        LV::ld_pair(QP, c.qoff[j], c.q[j], c.ph[j]);
+        if (later) LV::ld(R, k * Z + z, c.ro[j]);
+      }
+      LV::ld(S, static_cast<int>(se.y) + z - uj, c.sj[j]);
     }
   }
 }
 
-// Step 2 (1) b)-e) for the edges of a chunk, in ascending column order.
+// Step 2 (1) b)-e) for the edges of a chunk, in ascending column order.  Signs are
+// handled on the sign bits: no Q* is ever -0 (the channel LLRs are loaded as L + 0,
+// and a sum or difference of values that are not -0 is -0 only when both are -0 and
+// R^new is never -0), so the sign bit of Q* is [Q* < 0].
 template <int FPT, int CH>
 __device__ __forceinline__ void update_chunk(const Chunk<FPT, CH>& c, int kb, int k1,
                                              const int* t, float* Sacc, uint32_t* sig,
@@ -98,8 +102,8 @@ __device__ __forceinline__ void update_chunk(const Chunk<FPT, CH>& c, int kb, in
 #pragma unroll
   for (int j = 0; j < CH; ++j) {
     if (kb + j < k1) {
-      const bool self = c.fl[j] & kSelf;
-      const bool first_row = c.fl[j] & kFirst;
+      const bool self = c.fl[j] & kSpSelf;
+      const bool first_row = c.fl[j] & kSpFirst;
       float Rn[FPT], qn[FPT], phn[FPT];
       bool store_r = false;
 #pragma unroll
@@ -107,21 +111,89 @@ __device__ __forceinline__ void update_chunk(const Chunk<FPT, CH>& c, int kb, in
         // B2V, Eqs. (s4e18), (s4e13): exclude phi(|Q*|) from S of c_j; a variable not
         // visited before adds no C2V
         const float mag = phi_eval(fabsf(__fsub_rn(fabsf(c.sj[j][h]), c.ph[j][h])), xlo, tab);
-        const float rb = (sign_bit(c.sj[j][h]) ^ (c.q[j][h] < 0.0f)) ? -mag : mag;
+        const float rb = __uint_as_float(__float_as_uint(mag) |
+                                         ((__float_as_uint(c.sj[j][h]) ^
+                                           __float_as_uint(c.q[j][h])) & 0x80000000u));
         const bool first = (t[h] == 1) && first_row;
         Rn[h] = first ? 0.0f : rb;
         store_r |= !first;
         // V2C, Eqs. (s4e20), (s4e19); weight-1 column: c_j == c_i
         const float rold = self ? Rn[h] : (t[h] > 1 ? c.ro[j][h] : 0.0f);
         qn[h] = __fsub_rn(__fadd_rn(c.q[j][h], Rn[h]), rold);
-        // C2B, Eq. (s4e21) as a sum of phi
+        // C2B, Eq. (s4e21) as a sum of phi; the sign bits fold into sig
         phn[h] = phi_eval(fabsf(qn[h]), xlo, tab);
         Sacc[h] = __fadd_rn(Sacc[h], phn[h]);
-        sig[h] ^= (qn[h] < 0.0f);
+        sig[h] ^= __float_as_uint(qn[h]);
       }
-      if (store_r && !self) LV::st(R, c.roff[j], Rn);  // R_{c_j->v} <- R^new (Eq. s4e22)
-      LV::st_pair(self ? SV : QP, c.qoff[j], qn, phn);
+      if (self) {
+        LV::st_pair(SV, c.qoff[j], qn, phn);
+      } else {
+        if (store_r) LV::st(R, c.roff[j], Rn);  // R_{c_j->v} <- R^new (Eq. s4e22)
+        LV::st_pair(QP, c.qoff[j], qn, phn);
+      }
     }
+  }
+}
+
+// One base row of CH-edge chunks: loads of the next chunk are issued before the
+// current chunk's updates when DB (they never alias: a row reads its own R slots, the
+// beliefs of other rows and distinct variables, and writes predecessor R slots, its
+// variables and its own beliefs).
+template <int FPT, int CH, bool DB>
+__device__ __forceinline__ void row_edges(int k0, int k1, const SpEdge* __restrict__ s_spe,
+                                          int z, int Z, bool later, const int* t, float* Sacc,
+                                          uint32_t* sig, float xlo,
+                                          const float4* __restrict__ tab, float* QP, float* SV,
+                                          const float* S, float* R) {
+  if (DB) {
+    Chunk<FPT, CH> A, B;
+    load_chunk<FPT, CH>(A, k0, k1, s_spe, z, Z, later, QP, SV, S, R);
+    for (int kb = k0;;) {
+      if (kb + CH < k1) load_chunk<FPT, CH>(B, kb + CH, k1, s_spe, z, Z, later, QP, SV, S, R);
+      update_chunk<FPT, CH>(A, kb, k1, t, Sacc, sig, xlo, tab, QP, SV, R);
+      kb += CH;
+      if (kb >= k1) break;
+      if (kb + CH < k1) load_chunk<FPT, CH>(A, kb + CH, k1, s_spe, z, Z, later, QP, SV, S, R);
+      update_chunk<FPT, CH>(B, kb, k1, t, Sacc, sig, xlo, tab, QP, SV, R);
+      kb += CH;
+      if (kb >= k1) break;
+    }
+  } else {
+    for (int kb = k0; kb < k1; kb += CH) {
+      Chunk<FPT, CH> A;
+      load_chunk<FPT, CH>(A, kb, k1, s_spe, z, Z, later, QP, SV, S, R);
+      update_chunk<FPT, CH>(A, kb, k1, t, Sacc, sig, xlo, tab, QP, SV, R);
+    }
+  }
+}
+
+// Step 2 of one sweep: the base rows in order, one team barrier after each.
+template <int FPT, int CH, bool DB>
+__device__ __forceinline__ void sweep_rows(int mb, bool any, const int* s_rptr,
+                                        const SpEdge* __restrict__ s_spe, int z, int Z,
+                                        bool later, const int* t, float xlo,
+                                        const float4* __restrict__ tab, float* QP, float* SV,
+                                        float* S, float* R, int bar_id, int bar_n) {
+  using LV = Lanes<FPT>;
+  for (int r = 0; r < mb; ++r) {
+    if (any) {
+      const int k0 = s_rptr[r], k1 = s_rptr[r + 1];
+      float Sacc[FPT];
+      uint32_t sig[FPT];
+#pragma unroll
+      for (int h = 0; h < FPT; ++h) {
+        Sacc[h] = 0.0f;
+        sig[h] = 0;
+      }
+      row_edges<FPT, CH, DB>(k0, k1, s_spe, z, Z, later, t, Sacc, sig, xlo, tab, QP, SV,
+                                    S, R);
+      float sv[FPT];
+#pragma unroll
+      for (int h = 0; h < FPT; ++h)  // Sacc >= 0: its sign bit is free for sgn(Omega)
+        sv[h] = __uint_as_float(__float_as_uint(Sacc[h]) | (sig[h] & 0x80000000u));
+      LV::st(S, r * Z + z, sv);  // Eq. (s4e23); the sign bit carries sgn(Omega)
+    }
+    team_sync(bar_id, bar_n);
   }
 }
 
@@ -141,8 +213,8 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
   unsigned char* sp = smem;
   float4* s_tab = reinterpret_cast<float4*>(sp);
   sp += sizeof(float4) * kPhiSegments;
-  BaseEdge* s_e = reinterpret_cast<BaseEdge*>(sp);
-  sp += sizeof(BaseEdge) * p.nnzb;
+  SpEdge* s_spe = reinterpret_cast<SpEdge*>(sp);
+  sp += sizeof(SpEdge) * p.nnzb;
   int* s_rptr = reinterpret_cast<int*>(sp);
   sp += sizeof(int) * ((p.mb + 1 + 3) & ~3);
   uint2* s_col = reinterpret_cast<uint2*>(sp);  // (last row | shift << 16, idx | self << 16)
@@ -153,7 +225,7 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
 
   if (load_tab)
     for (int i = tid; i < kPhiSegments; i += blockDim.x) s_tab[i] = p.phi_tab[i];
-  for (int i = tid; i < p.nnzb; i += blockDim.x) s_e[i] = p.edges[i];
+  for (int i = tid; i < p.nnzb; i += blockDim.x) s_spe[i] = p.spe[i];
   for (int i = tid; i <= p.mb; i += blockDim.x) s_rptr[i] = p.rptr[i];
   for (int c = tid; c < p.nb; c += blockDim.x) {
     const ColEntry ce = p.cols[p.cptr[c + 1] - 1];
@@ -187,6 +259,7 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
   SlotState* my = s_slot + (lane ? g : 0) * FPT;
   const float4* tab = s_tab;
   const float xlo = p.phi_xlo;
+  const bool words_aligned = (Z & 31) == 0;
   // teams of p.team_groups lane groups (whole warps) synchronise among themselves
   const int tg = p.team_groups;
   const bool single_team = tg >= G || G * Z != static_cast<int>(blockDim.x);
@@ -210,9 +283,10 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
           const int idx = ci.y & 0xffff;
           if (ci.y & 0x10000u) {
             const int s = int(ci.x >> 16);
-            SV[((idx * Z + z) * FPT + h) * 2] = __ldg(src + c * Z + mod_add(z + s, Z));
+            SV[((idx * Z + z) * FPT + h) * 2] =
+                __fadd_rn(__ldg(src + c * Z + mod_add(z + s, Z)), 0.0f);  // -0 -> +0
           } else {
-            QP[((idx * Z + z) * FPT + h) * 2] = __ldg(src + c * Z + z);
+            QP[((idx * Z + z) * FPT + h) * 2] = __fadd_rn(__ldg(src + c * Z + z), 0.0f);
           }
         }
       }
@@ -223,48 +297,8 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
     bool later = false;  // some frame of the group is past its first sweep
 #pragma unroll
     for (int h = 0; h < FPT; ++h) later |= t[h] > 1;
-
-    for (int r = 0; r < p.mb; ++r) {
-      if (any) {
-        const int k0 = s_rptr[r], k1 = s_rptr[r + 1];
-        float Sacc[FPT];
-        uint32_t sig[FPT];
-#pragma unroll
-        for (int h = 0; h < FPT; ++h) {
-          Sacc[h] = 0.0f;
-          sig[h] = 0;
-        }
-        if (DB) {
-          // two register buffers: the next chunk's loads are issued before the current
-          // chunk's stores (they never alias: a row reads its own R slots, the beliefs of
-          // other rows and distinct variables, and writes predecessor R slots, its
-          // variables and its own beliefs)
-          Chunk<FPT, CH> A, B;
-          load_chunk<FPT, CH>(A, k0, k1, s_e, z, Z, later, QP, SV, S, R);
-          for (int kb = k0;;) {
-            if (kb + CH < k1) load_chunk<FPT, CH>(B, kb + CH, k1, s_e, z, Z, later, QP, SV, S, R);
-            update_chunk<FPT, CH>(A, kb, k1, t, Sacc, sig, xlo, tab, QP, SV, R);
-            kb += CH;
-            if (kb >= k1) break;
-            if (kb + CH < k1) load_chunk<FPT, CH>(A, kb + CH, k1, s_e, z, Z, later, QP, SV, S, R);
-            update_chunk<FPT, CH>(B, kb, k1, t, Sacc, sig, xlo, tab, QP, SV, R);
-            kb += CH;
-            if (kb >= k1) break;
-          }
-        } else {
-          for (int kb = k0; kb < k1; kb += CH) {
-            Chunk<FPT, CH> A;
-            load_chunk<FPT, CH>(A, kb, k1, s_e, z, Z, later, QP, SV, S, R);
-            update_chunk<FPT, CH>(A, kb, k1, t, Sacc, sig, xlo, tab, QP, SV, R);
-          }
-        }
-        float sv[FPT];
-#pragma unroll
-        for (int h = 0; h < FPT; ++h) sv[h] = sig[h] ? -Sacc[h] : Sacc[h];
-        LV::st(S, r * Z + z, sv);  // Eq. (s4e23); the sign bit carries sgn(Omega)
-      }
-      team_sync(bar_id, bar_n);
-    }
+    sweep_rows<FPT, CH, DB>(p.mb, any, s_rptr, s_spe, z, Z, later, t, xlo, tab, QP, SV, S, R,
+                            bar_id, bar_n);
 
     // ---- flushed posterior, hard decisions (Eq. s2e7)
 #pragma unroll
@@ -299,11 +333,32 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
         bool neg = false;
         if (act[h]) {
           const float mag = phi_eval(fabsf(__fsub_rn(fabsf(Sk[h]), pv[h])), xlo, tab);
-          const float lb = __fadd_rn(qv[h], (sign_bit(Sk[h]) ^ (qv[h] < 0.0f)) ? -mag : mag);
+          const float lb = __fadd_rn(
+              qv[h], __uint_as_float(__float_as_uint(mag) |
+                                     ((__float_as_uint(Sk[h]) ^ __float_as_uint(qv[h])) &
+                                      0x80000000u)));
           neg = lb < 0.0f;
           if (p.soft) p.soft[static_cast<long long>(frame[h]) * N + v] = lb;
         }
-        warp_or_bit(bits + h * wpad + (v >> 5), neg ? (1u << (v & 31)) : 0u, act[h]);
+        if (words_aligned) {
+          // Z % 32 == 0: a warp lies inside one lane group, and its 32 variables of
+          // column c are 32 consecutive positions of the column (rotated by the shift
+          // for a weight-1 column), i.e. one aligned word or two partial ones
+          const unsigned wv = __ballot_sync(0xffffffffu, neg);
+          if ((tid & 31) == 0 && act[h]) {
+            uint32_t* wb = bits + h * wpad;
+            const int p0 = v - c * Z;  // position of this lane's variable in column c
+            const int sh = p0 & 31;
+            if (sh == 0) {
+              wb[v >> 5] = wv;  // the word holds exactly this warp's variables
+            } else {
+              atomicOr(wb + (v >> 5), wv << sh);
+              atomicOr(wb + ((c * Z + mod_add(p0 - sh + 32, Z)) >> 5), wv >> (32 - sh));
+            }
+          }
+        } else {
+          warp_or_bit(bits + h * wpad + (v >> 5), neg ? (1u << (v & 31)) : 0u, act[h]);
+        }
       }
     }
     team_sync(bar_id, bar_n);
@@ -321,7 +376,7 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
 #pragma unroll
         for (int h = 0; h < FPT; ++h) pr[h] = 0;
         for (int k = s_rptr[r]; k < s_rptr[r + 1]; ++k) {
-          const BaseEdge be = s_e[k];
+          const BaseEdge be = p.edges[k];  // read through L1: the scan is off the hot path
           const int v = be.c * Z + mod_add(z + be.s, Z);
 #pragma unroll
           for (int h = 0; h < FPT; ++h) pr[h] ^= bits[h * wpad + (v >> 5)] >> (v & 31);
