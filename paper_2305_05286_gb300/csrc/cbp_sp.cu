@@ -167,6 +167,18 @@ __device__ __forceinline__ void row_edges(int k0, int k1, const SpEdge* __restri
   }
 }
 
+constexpr int kPrefetchRows = 1;
+
+// Bulk prefetch of [a, b) into L2, shrunk to whole 16-byte units inside the range.
+__device__ __forceinline__ void prefetch_l2(const float* a, const float* b) {
+  const uintptr_t lo = (reinterpret_cast<uintptr_t>(a) + 15) & ~uintptr_t(15);
+  const uintptr_t hi = reinterpret_cast<uintptr_t>(b) & ~uintptr_t(15);
+  if (hi > lo)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo),
+                 "r"(static_cast<uint32_t>(hi - lo))
+                 : "memory");
+}
+
 // Step 2 of one sweep: the base rows in order, one team barrier after each.
 template <int FPT, int CH, bool DB>
 __device__ __forceinline__ void sweep_rows(int mb, bool any, const int* s_rptr,
@@ -178,6 +190,16 @@ __device__ __forceinline__ void sweep_rows(int mb, bool any, const int* s_rptr,
   for (int r = 0; r < mb; ++r) {
     if (any) {
       const int k0 = s_rptr[r], k1 = s_rptr[r + 1];
+      if (later && z == 0) {
+        // the C2V slots of base row r + kPrefetchRows (cyclically) are contiguous in the
+        // workspace: one bulk L2 prefetch per lane group brings them on chip while this
+        // row runs (a non-binding hint; rows in between may still rewrite those lines)
+        int rn = r + kPrefetchRows;
+        rn = rn >= mb ? rn - mb : rn;
+        const float* a = R + static_cast<long long>(s_rptr[rn]) * Z * FPT;
+        const float* b = R + static_cast<long long>(s_rptr[rn + 1]) * Z * FPT;
+        prefetch_l2(a, b);
+      }
       float Sacc[FPT];
       uint32_t sig[FPT];
 #pragma unroll
