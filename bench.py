@@ -39,6 +39,11 @@ MAX_ITER = 20
 OPS_EDGE = {"cbp_sp": 64, "cbp_nms": 31, "lbp_nms": 28, "fbp_sp": 64}
 OPS_VAR = {"cbp_sp": 30, "cbp_nms": 10, "lbp_nms": 3, "fbp_sp": 5}
 OPS_SYN = 4
+# DRAM bytes (read + write) per frame-sweep of the CBP-SP kernel on the 26112-bit code, from
+# one ncu capture of 2432 frames (14.04 GB over 9699 frame-sweeps); the workspace traffic
+# grows with frame-sweeps, so a launch's traffic is this times its frame-sweeps.
+TRAFFIC_PER_FRAME_SWEEP = {"cbp_sp": 14.04e9 / (2432 * 3.98808)}
+TRAFFIC_SOURCE = "profiles/cbp_sp_kernel_n26112_2432frames.md, scaled by frame-sweeps"
 
 
 def load_peaks():
@@ -253,8 +258,13 @@ def run_ours(args, rank, world, dist):
     peak_ops = sms * 128 * sm_mhz * 1e6 / 1e12  # T lane-ops/s at the sampled SM clock
     ops = alu_ops(args.alg, qc, st["sweeps_total"])
     achieved = ops / (ms / 1e3) / 1e12
+    traffic, traffic_src = args.traffic, "--traffic"
+    if traffic is None and args.alg in TRAFFIC_PER_FRAME_SWEEP:
+        frame_sweeps = st["sweeps_total"]
+        traffic = TRAFFIC_PER_FRAME_SWEEP[args.alg] * frame_sweeps
+        traffic_src = TRAFFIC_SOURCE
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "T issue-slots/s",
-                "frac": achieved / peak_ops, "traffic": args.traffic,
+                "frac": achieved / peak_ops, "traffic": traffic, "traffic_source": traffic_src,
                 "peak_source": f"{sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (sampled SM clock)",
                 "units": {"edge_sweeps": qc.E * st["sweeps_total"],
                           "ops_per_edge": OPS_EDGE[args.alg] + OPS_SYN,
@@ -262,6 +272,16 @@ def run_ours(args, rank, world, dist):
     hbm_bytes = B * (4 * qc.N + 4 * code.words + 4)
     roofline["hbm_algorithmic_GBs"] = hbm_bytes / (ms / 1e3) / 1e9
     roofline["hbm_peak_GBs"] = peaks.get("hbm_gbs")
+    if args.alg == "cbp_sp":
+        # measured compute ceiling: the CBP-SP edge update from registers, same phi
+        ceil = cbp.edge_ceiling(iters=2048)
+        rate = qc.E * st["sweeps_total"] / (ms / 1e3)
+        roofline["edge_ceiling"] = {
+            "ceiling_edge_updates_per_s": ceil["edge_updates_per_s"],
+            "decoder_edge_updates_per_s": rate,
+            "frac": rate / ceil["edge_updates_per_s"],
+            "note": "cbp_edge_ceiling: 4 independent edge updates per thread, registers only, "
+                    "phi table in shared memory, full occupancy"}
 
     comparators = {}
     if not args.no_comparators:

@@ -255,6 +255,21 @@ int cbp_decode_multi(const cbp_multi_item_t* items, int n_items, int max_iter,
  * on n device values: y[i] = phi(x[i]).  x, y device, 4-byte aligned, n >= 0. */
 int cbp_phi(const float* x, float* y, int64_t n, cbp_stream_t stream);
 
+/* Measurement helper (no counterpart in the paper): the compute ceiling of the CBP-SP
+ * edge update.  Launches `ctas` CTAs of 512 threads (ctas <= 0: every SM filled to its
+ * occupancy limit) in which each thread runs `iters` rounds of 4 independent edge updates
+ * of Sec. IV-C Step 2 -- B2V (Eqs. s4e18, s4e13) with phi, V2C (s4e20, s4e19), C2B
+ * (s4e21) with phi and the check-belief fold -- on register-resident values, with the
+ * decoders' phi (table in shared memory).  No other memory is touched, so the edge
+ * updates per second it reaches bound the decoder's from above.  *edge_updates receives
+ * the number of edge updates the launch performs; time it with events on `stream`.
+ *   sink        device array of sink_floats floats, >= (CTAs launched) * 512 (written
+ *               only in a case that does not occur; it keeps the work observable)
+ *   ctas_used   optional: the number of CTAs launched
+ * Asynchronous; errors: CBP_EINVAL (iters < 1, NULL pointers, sink too small), CBP_ECUDA. */
+int cbp_edge_ceiling(int ctas, int iters, float* sink, size_t sink_floats, cbp_stream_t stream,
+                     int64_t* edge_updates, int* ctas_used);
+
 /* Static description of an error code. */
 const char* cbp_strerror(int status);
 

@@ -27,7 +27,7 @@ EXPORTS = ("cbp_code_create", "cbp_code_destroy", "cbp_code_info", "cbp_workspac
            "cbp_launch_info", "cbp_decode", "cbp_decode_ex", "cbp_grad_workspace_bytes",
            "cbp_decode_weighted", "cbp_decode_grad", "cbp_decode_noalloc",
            "cbp_multi_workspace_bytes", "cbp_multi_launch_info", "cbp_decode_multi", "cbp_phi",
-           "cbp_strerror")
+           "cbp_edge_ceiling", "cbp_strerror")
 MULTI_MAX_ITEMS = 8
 
 
@@ -96,6 +96,8 @@ def lib(build_if_needed: bool = True):
             L.cbp_decode_multi.argtypes = [MI, I, I, P, Z, P, MO]
             L.cbp_phi.restype = I
             L.cbp_phi.argtypes = [P, P, C.c_int64, P]
+            L.cbp_edge_ceiling.restype = I
+            L.cbp_edge_ceiling.argtypes = [I, I, P, Z, P, C.POINTER(C.c_int64), C.POINTER(I)]
             L.cbp_strerror.restype = C.c_char_p
             L.cbp_strerror.argtypes = [I]
             _lib = L
@@ -228,6 +230,28 @@ def phi(x: torch.Tensor, stream=None) -> torch.Tensor:
     y = torch.empty_like(x)
     _check("cbp_phi", lib().cbp_phi(x.data_ptr(), y.data_ptr(), x.numel(), _stream_ptr(stream)))
     return y
+
+
+def edge_ceiling(iters: int = 4096, ctas: int = 0, stream=None) -> dict:
+    """Time the CBP-SP edge-update ceiling kernel (cbp_edge_ceiling) with CUDA events:
+    edge updates per second with every SM filled to its occupancy limit (ctas = 0)."""
+    L = lib()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    n, used = C.c_int64(), C.c_int()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    # 512-thread CTAs: at most 2048 / 512 = 4 per SM
+    sink = torch.empty((ctas if ctas > 0 else 4 * sms) * 512, dtype=torch.float32, device="cuda")
+    args = lambda it: (int(ctas), int(it), sink.data_ptr(), sink.numel(), int(st.cuda_stream),
+                       C.byref(n), C.byref(used))
+    _check("cbp_edge_ceiling", L.cbp_edge_ceiling(*args(16)))  # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    _check("cbp_edge_ceiling", L.cbp_edge_ceiling(*args(iters)))
+    e1.record(st)
+    e1.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    return {"edge_updates_per_s": n.value / secs, "ctas": used.value, "iters": int(iters),
+            "seconds": secs}
 
 
 def unpack_bits(words: torch.Tensor, N: int) -> torch.Tensor:

@@ -1034,6 +1034,26 @@ int cbp_phi(const float* x, float* y, int64_t n, cbp_stream_t stream) {
              : CBP_ECUDA;
 }
 
+int cbp_edge_ceiling(int ctas, int iters, float* sink, size_t sink_floats, cbp_stream_t stream,
+                     int64_t* edge_updates, int* ctas_used) {
+  if (iters < 1 || !sink || !edge_updates || !aligned(sink, 4)) return CBP_EINVAL;
+  DeviceInfo* di = nullptr;
+  if (int rc = current_device(&di, nullptr)) return rc;
+  if (ctas <= 0) {
+    int per_sm = 0;
+    if (edge_ceiling_ctas_per_sm(&per_sm) || per_sm < 1) return CBP_ECUDA;
+    ctas = per_sm * di->sms;
+  }
+  if (static_cast<size_t>(ctas) * 512 > sink_floats) return CBP_EINVAL;
+  long long edges = 0;
+  if (launch_edge_ceiling(di->tab, di->xlo, ctas, iters, sink,
+                          reinterpret_cast<cudaStream_t>(stream), &edges) != cudaSuccess)
+    return CBP_ECUDA;
+  *edge_updates = edges;
+  if (ctas_used) *ctas_used = ctas;
+  return CBP_OK;
+}
+
 const char* cbp_strerror(int s) {
   switch (s) {
     case CBP_OK: return "success";

@@ -187,6 +187,10 @@ void* minsum_kernel_ptr(int alg, bool chk_shared);          // cbp_minsum.cu
 void* flood_kernel_ptr();              // cbp_flood.cu
 cudaError_t launch_phi(const float* x, float* y, long long n, const float4* tab, float xlo,
                        cudaStream_t st);
+// CBP-SP edge-update ceiling (cbp_ceiling.cu): 512 threads per CTA.
+cudaError_t launch_edge_ceiling(const float4* tab, float xlo, int blocks, int iters,
+                                float* sink, cudaStream_t st, long long* edges);
+int edge_ceiling_ctas_per_sm(int* ctas);
 
 // Weighted CBP (differentiable decoder), cbp_grad.cu.
 struct GParams {

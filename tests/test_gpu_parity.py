@@ -211,3 +211,16 @@ def test_wide_rows_cbp_only():
     llr = (3.0 + 2.0 * rng.standard_normal((40, qc.N))).astype(np.float32)
     for alg in ("cbp_sp", "cbp_nms"):
         assert_parity(run_gpu(code, llr, alg, max_iter=8), oc.decode(llr, alg=alg, max_iter=8), alg)
+
+
+def test_edge_ceiling_runs_and_checks_its_sink():
+    import ctypes as C
+    r = cbp.edge_ceiling(iters=64)
+    assert r["ctas"] >= torch.cuda.get_device_properties(0).multi_processor_count
+    assert r["edge_updates_per_s"] > 1e9
+    n, used = C.c_int64(), C.c_int()
+    small = torch.empty(512, dtype=torch.float32, device="cuda")
+    rc = cbp.lib().cbp_edge_ceiling(2, 8, small.data_ptr(), small.numel(), None, C.byref(n),
+                                    C.byref(used))
+    assert rc == -1 and n.value == 0   # two CTAs need 1024 sink floats: nothing launched
+    torch.cuda.synchronize()
