@@ -249,6 +249,7 @@ def run_ours(args, rank, world, dist):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     st = frame_stats(torch, cbp, qc, hard, iters, cw)
+    iters_dev = iters.cpu()  # for the end-to-end run's check (comparators reuse `iters`)
     value = world * K * B / (ms / 1e3) / 1e9
 
     peaks = load_peaks()
@@ -306,15 +307,12 @@ def run_ours(args, rank, world, dist):
     if not args.no_e2e:
         host = torch.empty((B, qc.N), dtype=torch.float32, pin_memory=True)
         host.copy_(llr)
-        x = torch.empty_like(llr)
         hard_h = torch.empty((B, code.words), dtype=torch.int32, pin_memory=True)
         iters_h = torch.empty((B,), dtype=torch.int32, pin_memory=True)
 
-        def e2e_step():
-            x.copy_(host, non_blocking=True)
-            code.decode_into(x, hard, iters, max_iter=MAX_ITER, alg=args.alg, workspace=ws)
-            hard_h.copy_(hard, non_blocking=True)
-            iters_h.copy_(iters, non_blocking=True)
+        def e2e_step():  # cbp_decode_host: chunked H2D / decode / D2H, copies overlapped
+            code.decode_host(host, max_iter=MAX_ITER, alg=args.alg, chunk=args.e2e_chunk,
+                             hard=hard_h, iters=iters_h, sync=False)
 
         e2e_step()
         torch.cuda.synchronize()
@@ -327,8 +325,10 @@ def run_ours(args, rank, world, dist):
             ems = float(t.item())
         e2e = {"value": world * K * B / (ems / 1e3) / 1e9, "unit": "Gbit/s",
                "h2d_bytes_per_step": B * qc.N * 4,
-               "d2h_bytes_per_step": B * code.words * 4 + B * 4, "ms_per_step": ems}
-        del host, hard_h, iters_h, x
+               "d2h_bytes_per_step": B * code.words * 4 + B * 4, "ms_per_step": ems,
+               "api": f"Code.decode_host (cbp_decode_host), chunks of {args.e2e_chunk} frames",
+               "check_iters_equal_device_run": bool(torch.equal(iters_h, iters_dev))}
+        del host, hard_h, iters_h
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -565,6 +565,36 @@ def run_multi_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def run_nms_study(args):
+    """CBP min-sum against CBP log-tanh: FER, BER and mean sweeps over an Eb/N0 grid on the
+    576- and 2304-bit codes, CBP-NMS for several normalisations alpha, with layered NMS and
+    flooding BP beside them (30 sweeps at most, syndrome stop)."""
+    import torch
+
+    from paper_2305_05286_gb300 import cbp
+    from paper_2305_05286_gb300 import inputs as I
+
+    alphas = [float(a) for a in args.alphas.split(",")]
+    for name, qc in (("n576", I.code_576()), ("n2304", I.code_2304())):
+        code = cbp.Code.from_qc(qc)
+        B = args.study_frames
+        for pi, e in enumerate(np.arange(args.sweep_lo, args.sweep_hi + 1e-9, 0.25)):
+            llr, cw = I.make_frames_torch(qc, B, float(e), seed=7000 + 100 * pi + qc.Z)
+            hard = torch.empty((B, code.words), dtype=torch.int32, device="cuda")
+            iters = torch.empty((B,), dtype=torch.int32, device="cuda")
+            runs = [("cbp_sp", 0.75), ("fbp_sp", 0.75), ("lbp_nms", 0.75)]
+            runs += [("cbp_nms", a) for a in alphas]
+            for alg, a in runs:
+                code.decode_into(llr, hard, iters, max_iter=30, alg=alg, alpha=a,
+                                 workspace=code.workspace(B, alg))
+                s = frame_stats(torch, cbp, qc, hard, iters, cw)
+                print(json.dumps({"code": name, "ebn0_db": round(float(e), 2), "alg": alg,
+                                  "alpha": a if "nms" in alg else None, "frames": B,
+                                  "fer": s["fer"], "ber": s["ber"],
+                                  "mean_iters": s["mean_iters"]}), flush=True)
+            del llr, cw
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -578,6 +608,9 @@ def main():
     ap.add_argument("--sweep-frames", type=int, default=16384)
     ap.add_argument("--learned", action="store_true")
     ap.add_argument("--multi", action="store_true")
+    ap.add_argument("--nms-study", action="store_true")
+    ap.add_argument("--study-frames", type=int, default=100000)
+    ap.add_argument("--alphas", default="0.625,0.6875,0.75,0.8125,0.875,1.0")
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--train-frames", type=int, default=8192)
     ap.add_argument("--eval-frames", type=int, default=1_000_000)
@@ -586,6 +619,7 @@ def main():
     ap.add_argument("--sweep-hi", type=float, default=2.0)
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-chunk", type=int, default=8192)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-frames", type=int, default=4096)
@@ -613,6 +647,8 @@ def main():
         run_learned(args)
     elif args.multi:
         run_multi_bench(args)
+    elif args.nms_study:
+        run_nms_study(args)
     else:
         run_ours(args, rank, world, dist)
     if dist:

@@ -121,6 +121,27 @@ int cbp_decode_ex(const cbp_code_t* code, const float* llr, uint32_t* hard_out,
                   int32_t* iters_out, int max_iter, int batch, void* workspace,
                   size_t workspace_bytes, cbp_stream_t stream, const cbp_opts_t* opts);
 
+/* ---- Decoding from host memory, copies overlapped with decoding -------------------
+ * The same decode as cbp_decode_ex, with the LLRs and the results in host memory.  The
+ * batch is cut into chunks of `chunk` frames; while chunk i is decoded on `stream`,
+ * chunk i + 1 is copied in (and chunk i - 1's results out) on a second stream that the
+ * call creates and releases.  Two chunk buffers live in the caller's device memory
+ * `dev_buf` of at least cbp_host_buffer_bytes(code, chunk, opts) bytes (256-byte
+ * aligned); the library allocates no device memory.  The paper has no counterpart.
+ *   llr_host    host [batch][N] fp32; hard_host [batch][ceil(N/32)] uint32;
+ *   iters_host  host [batch] int32.  Page-locked (pinned) host memory is needed for the
+ *               copies to overlap the decoding; other host memory works but serialises.
+ *   chunk       frames per chunk, >= 1 (chunks of a few times the frame slots in flight
+ *               keep the launch tails short)
+ * opts->soft_out must be NULL (no soft output from this entry point).  Asynchronous on
+ * `stream`: the host buffers must stay valid until `stream` has completed the work.
+ * Errors as cbp_decode_ex, and CBP_EWORKSPACE if dev_buf is too small. */
+int cbp_host_buffer_bytes(const cbp_code_t* code, int chunk, const cbp_opts_t* opts,
+                          size_t* bytes);
+int cbp_decode_host(const cbp_code_t* code, const float* llr_host, uint32_t* hard_host,
+                    int32_t* iters_host, int max_iter, int batch, int chunk, void* dev_buf,
+                    size_t dev_bytes, cbp_stream_t stream, const cbp_opts_t* opts);
+
 /* The launch a decode of `batch` frames with `opts` would use (for tuning and reports):
  *   info[0] resident frames per SM      info[1] threads per CTA
  *   info[2] CTAs per SM                 info[3] lane groups per CTA

@@ -24,7 +24,8 @@ STATUS = {0: "CBP_OK", -1: "CBP_EINVAL", -2: "CBP_ENOMEM", -3: "CBP_ECUDA",
 
 # Every symbol include/cbp.h declares (checked by the ABI test).
 EXPORTS = ("cbp_code_create", "cbp_code_destroy", "cbp_code_info", "cbp_workspace_bytes",
-           "cbp_launch_info", "cbp_decode", "cbp_decode_ex", "cbp_grad_workspace_bytes",
+           "cbp_launch_info", "cbp_decode", "cbp_decode_ex", "cbp_host_buffer_bytes",
+           "cbp_decode_host", "cbp_grad_workspace_bytes",
            "cbp_decode_weighted", "cbp_decode_grad", "cbp_decode_noalloc",
            "cbp_multi_workspace_bytes", "cbp_multi_launch_info", "cbp_decode_multi", "cbp_phi",
            "cbp_edge_ceiling", "cbp_strerror")
@@ -79,6 +80,10 @@ def lib(build_if_needed: bool = True):
             L.cbp_decode.argtypes = [P, P, P, P, I, I, P, Z, P]
             L.cbp_decode_ex.restype = I
             L.cbp_decode_ex.argtypes = [P, P, P, P, I, I, P, Z, P, C.POINTER(_Opts)]
+            L.cbp_host_buffer_bytes.restype = I
+            L.cbp_host_buffer_bytes.argtypes = [P, I, C.POINTER(_Opts), C.POINTER(Z)]
+            L.cbp_decode_host.restype = I
+            L.cbp_decode_host.argtypes = [P, P, P, P, I, I, I, P, Z, P, C.POINTER(_Opts)]
             L.cbp_grad_workspace_bytes.restype = I
             L.cbp_grad_workspace_bytes.argtypes = [P, I, I, I, C.POINTER(Z)]
             L.cbp_decode_weighted.restype = I
@@ -220,6 +225,44 @@ class Code:
                 torch.cuda.current_stream(dev).synchronize()
             return hard_h, iters_h, sb_h
         return hard, iters, sb
+
+    def decode_host(self, llr: torch.Tensor, max_iter: int = 30, alg: str = "cbp_sp",
+                     alpha: float = 0.75, stop: str = "syndrome", chunk: int = 16384,
+                     hard: torch.Tensor | None = None, iters: torch.Tensor | None = None,
+                     stream=None, sync: bool = True):
+        """Decode host LLRs [B, N] float32 with the copies overlapped with decoding
+        (cbp_decode_host).  Page-locked ``llr`` (and outputs) let the copies overlap.  Returns
+        host (hard int32 [B, ceil(N/32)], iters int32 [B]); with ``sync`` the call waits for
+        the stream."""
+        if llr.is_cuda or llr.dtype != torch.float32 or not llr.is_contiguous():
+            raise ValueError("llr must be a contiguous float32 host tensor")
+        B = llr.shape[0]
+        if llr.numel() != B * self.N:
+            raise ValueError(f"llr must have {self.N} values per frame")
+        pin = llr.is_pinned()
+        if hard is None:
+            hard = torch.empty((B, self.words), dtype=torch.int32, pin_memory=pin)
+        if iters is None:
+            iters = torch.empty((B,), dtype=torch.int32, pin_memory=pin)
+        if hard.is_cuda or iters.is_cuda or hard.numel() < B * self.words or iters.numel() < B:
+            raise ValueError("hard/iters must be host tensors large enough for the batch")
+        chunk = max(1, min(int(chunk), max(B, 1)))
+        o = _opts(alg, alpha, stop, None)
+        need = C.c_size_t()
+        _check("cbp_host_buffer_bytes",
+               lib().cbp_host_buffer_bytes(self._h, chunk, C.byref(o), C.byref(need)))
+        buf = getattr(self, "_hbuf", None)
+        if buf is None or buf.numel() < need.value:
+            buf = torch.empty(max(need.value, 256), dtype=torch.uint8, device=f"cuda:{self.device}")
+            self._hbuf = buf
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        _check("cbp_decode_host",
+               lib().cbp_decode_host(self._h, llr.data_ptr(), hard.data_ptr(), iters.data_ptr(),
+                                     int(max_iter), int(B), chunk, buf.data_ptr(), buf.numel(),
+                                     int(st.cuda_stream), C.byref(o)))
+        if sync:
+            st.synchronize()
+        return hard, iters
 
 
 def phi(x: torch.Tensor, stream=None) -> torch.Tensor:

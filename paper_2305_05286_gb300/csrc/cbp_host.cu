@@ -672,6 +672,139 @@ int cbp_decode(const cbp_code_t* c, const float* llr, uint32_t* hard_out, int32_
 }
 
 // ---------------------------------------------------------------------------
+// Decoding from host memory with the copies overlapped (two chunk buffers).
+// ---------------------------------------------------------------------------
+namespace {
+
+struct HostLayout {
+  size_t llr[2], hard[2], iters[2], ws, total;
+};
+
+size_t round256(size_t n) { return (n + 255) & ~static_cast<size_t>(255); }
+
+HostLayout host_layout(const cbp_code* c, int chunk, size_t ws_bytes) {
+  HostLayout L{};
+  const size_t words = (static_cast<size_t>(c->N) + 31) / 32;
+  size_t off = 0;
+  for (int b = 0; b < 2; ++b) {
+    L.llr[b] = off;
+    off += round256(static_cast<size_t>(chunk) * c->N * sizeof(float));
+  }
+  for (int b = 0; b < 2; ++b) {
+    L.hard[b] = off;
+    off += round256(static_cast<size_t>(chunk) * words * sizeof(uint32_t));
+  }
+  for (int b = 0; b < 2; ++b) {
+    L.iters[b] = off;
+    off += round256(static_cast<size_t>(chunk) * sizeof(int32_t));
+  }
+  L.ws = off;
+  L.total = off + ws_bytes;
+  return L;
+}
+
+int host_setup(const cbp_code* c, int chunk, const cbp_opts_t* opts, int* alg, float* alpha,
+               int* stop, DeviceInfo** dio, Plan* pl, HostLayout* L) {
+  if (!c || chunk < 1) return CBP_EINVAL;
+  float* soft = nullptr;
+  if (int rc = check_opts(opts, alg, alpha, stop, &soft)) return rc;
+  if (soft) return CBP_EINVAL;
+  int dev = 0;
+  if (int rc = current_device(dio, &dev)) return rc;
+  if (dev != c->dev) return CBP_EDEVICE;
+  if (int rc = make_plan(c, **dio, *alg, chunk, pl)) return rc;
+  *L = host_layout(c, chunk, pl->ws_bytes);
+  return CBP_OK;
+}
+
+}  // namespace
+
+int cbp_host_buffer_bytes(const cbp_code_t* c, int chunk, const cbp_opts_t* opts,
+                          size_t* bytes) {
+  if (!bytes) return CBP_EINVAL;
+  int alg, stop;
+  float alpha;
+  DeviceInfo* di = nullptr;
+  Plan pl;
+  HostLayout L;
+  if (int rc = host_setup(c, chunk, opts, &alg, &alpha, &stop, &di, &pl, &L)) return rc;
+  *bytes = L.total;
+  return CBP_OK;
+}
+
+int cbp_decode_host(const cbp_code_t* c, const float* llr_host, uint32_t* hard_host,
+                    int32_t* iters_host, int max_iter, int batch, int chunk, void* dev_buf,
+                    size_t dev_bytes, cbp_stream_t stream, const cbp_opts_t* opts) {
+  if (!c || max_iter < 1 || batch < 0) return CBP_EINVAL;
+  int alg, stop;
+  float alpha;
+  DeviceInfo* di = nullptr;
+  Plan pl;
+  HostLayout L;
+  if (int rc = host_setup(c, chunk, opts, &alg, &alpha, &stop, &di, &pl, &L)) return rc;
+  if (batch == 0) return CBP_OK;
+  if (!llr_host || !hard_host || !iters_host || !dev_buf || !aligned(dev_buf, 256))
+    return CBP_EINVAL;
+  if (dev_bytes < L.total) return CBP_EWORKSPACE;
+  unsigned char* base = static_cast<unsigned char*>(dev_buf);
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t words = (static_cast<size_t>(c->N) + 31) / 32;
+  const int n_chunks = static_cast<int>((static_cast<long long>(batch) + chunk - 1) / chunk);
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_dec[2] = {nullptr, nullptr}, ev_done = nullptr;
+  int rc = CBP_OK;
+  auto ok = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == CBP_OK) rc = CBP_ECUDA;
+    return rc == CBP_OK;
+  };
+  auto frames = [&](int i) { return std::min(chunk, batch - i * chunk); };
+  auto h2d = [&](int i) {
+    const int b = i & 1;
+    return ok(cudaMemcpyAsync(base + L.llr[b], llr_host + static_cast<size_t>(i) * chunk * c->N,
+                              static_cast<size_t>(frames(i)) * c->N * sizeof(float),
+                              cudaMemcpyHostToDevice, cs)) &&
+           ok(cudaEventRecord(ev_in[b], cs));
+  };
+  if (ok(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) &&
+      ok(cudaEventCreateWithFlags(&ev_in[0], cudaEventDisableTiming)) &&
+      ok(cudaEventCreateWithFlags(&ev_in[1], cudaEventDisableTiming)) &&
+      ok(cudaEventCreateWithFlags(&ev_dec[0], cudaEventDisableTiming)) &&
+      ok(cudaEventCreateWithFlags(&ev_dec[1], cudaEventDisableTiming)) &&
+      ok(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming))) {
+    // the copy stream starts after the work the caller queued on `stream` before this call
+    ok(cudaEventRecord(ev_done, st)) && ok(cudaStreamWaitEvent(cs, ev_done, 0));
+    for (int i = 0; i < std::min(2, n_chunks) && rc == CBP_OK; ++i) h2d(i);
+    for (int i = 0; i < n_chunks && rc == CBP_OK; ++i) {
+      const int b = i & 1, n = frames(i);
+      KParams p = code_params(c, *di, pl, n, max_iter, stop, alpha);
+      p.llr = reinterpret_cast<const float*>(base + L.llr[b]);
+      p.hard = reinterpret_cast<uint32_t*>(base + L.hard[b]);
+      p.iters = reinterpret_cast<int32_t*>(base + L.iters[b]);
+      p.ws = reinterpret_cast<float*>(base + L.ws);
+      if (!ok(cudaStreamWaitEvent(st, ev_in[b], 0)) ||
+          !ok(launch_decoder(pl.v, p, pl.grid, pl.threads, pl.smem, st)) ||
+          !ok(cudaEventRecord(ev_dec[b], st)) || !ok(cudaStreamWaitEvent(cs, ev_dec[b], 0)) ||
+          !ok(cudaMemcpyAsync(hard_host + static_cast<size_t>(i) * chunk * words,
+                              base + L.hard[b], static_cast<size_t>(n) * words * sizeof(uint32_t),
+                              cudaMemcpyDeviceToHost, cs)) ||
+          !ok(cudaMemcpyAsync(iters_host + static_cast<size_t>(i) * chunk, base + L.iters[b],
+                              static_cast<size_t>(n) * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                              cs)))
+        break;
+      // buffer b is free again once chunk i is decoded and its results copied out
+      if (i + 2 < n_chunks) h2d(i + 2);
+    }
+    // `stream` completes after the last copy
+    if (rc == CBP_OK) ok(cudaEventRecord(ev_done, cs)) && ok(cudaStreamWaitEvent(st, ev_done, 0));
+  }
+  // released once the queued work has finished
+  for (cudaEvent_t e : {ev_in[0], ev_in[1], ev_dec[0], ev_dec[1], ev_done})
+    if (e) cudaEventDestroy(e);
+  if (cs) cudaStreamDestroy(cs);
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
 // Weighted CBP (differentiable decoder)
 // ---------------------------------------------------------------------------
 namespace {

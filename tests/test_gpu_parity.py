@@ -224,3 +224,27 @@ def test_edge_ceiling_runs_and_checks_its_sink():
                                     C.byref(used))
     assert rc == -1 and n.value == 0   # two CTAs need 1024 sink floats: nothing launched
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("chunk", [1, 7, 100, 5000])
+def test_decode_host_matches_device_decode(code576, chunk):
+    qc, code, _ = code576
+    fr = I.make_frames(qc, 333, 1.75, seed=4242)
+    host = torch.from_numpy(fr.llr).pin_memory()
+    for alg in ("cbp_sp", "lbp_nms"):
+        h_ref, i_ref, _ = code.decode(host.cuda(), max_iter=20, alg=alg)
+        h, i = code.decode_host(host, max_iter=20, alg=alg, chunk=chunk)
+        assert not h.is_cuda and torch.equal(i, i_ref.cpu()) and torch.equal(h, h_ref.cpu())
+    # pageable host memory works too (copies serialise)
+    h, i = code.decode_host(torch.from_numpy(fr.llr), max_iter=20, chunk=64)
+    h_ref, i_ref, _ = code.decode(host.cuda(), max_iter=20)
+    assert torch.equal(i, i_ref.cpu()) and torch.equal(h, h_ref.cpu())
+
+
+@pytest.mark.parametrize("alpha", [0.625, 0.8125, 1.0])
+def test_min_sum_normalisations(code576, alpha):
+    qc, code, oc = code576
+    fr = I.make_frames(qc, 400, 2.25, seed=900 + int(alpha * 1000))
+    for alg in ("cbp_nms", "lbp_nms"):
+        ref = oc.decode(fr.llr, alg=alg, max_iter=30, alpha=alpha, threads=THREADS)
+        assert_parity(run_gpu(code, fr.llr, alg, alpha=alpha), ref, f"{alg} alpha {alpha}")
