@@ -34,6 +34,13 @@
 //     full sweep on the flushed posterior Lambda_bar_v = Q_v + B2V(last check of v, v),
 //     a read-only evaluation of Eq. (s4e20) at the end of the sweep.  iters = sweeps run,
 //     negated when the syndrome is still non-zero after max_iter sweeps.
+//   * Paper-literal stop (CBP log-tanh only): Eq. (s4e24) read as a window of M
+//     consecutive check updates (the check-beliefs number M, not N), counted across
+//     sweep boundaries, each leaving Omega > 0 (Eq. s4e2) and no flip of a posterior
+//     sign of Eq. (s4e20) against that variable's previous posterior (initially the
+//     channel LLR).  Decoding stops right after the M-th such update, possibly in the
+//     middle of a sweep; the output is the sign of each variable's latest Lambda^new
+//     (Step 3, "generated in the V2C phase").
 //   * CBP min-sum: minima of |Q| kept unscaled; strict '<' so the first of equal values
 //     wins; B2V picks min2 when |Q*_v| equals min1; R = alpha * min with sign.
 //   * phi in FP32: phi(clamp(x, X_LO, X_HI)), X_HI = 30, X_LO = fl32(phi(30)),
@@ -214,11 +221,24 @@ struct Frame {
     sg.assign(M, 0);
     R.assign(E, T(0));                 // Eq. (s4e17)
     last.assign(N, -1);                // edge of the latest updated check of v
+    // Paper-literal stop (stop == 2), Step 2 (3) and Step 3 of Sec. IV-C: the decoding
+    // succeeds once M consecutive check updates each leave Omega > 0 (Eq. s4e2) and flip
+    // no posterior sign of Eq. (s4e20) (Eq. s4e24); the output is the hard decision of
+    // the latest V2C phase.  pneg[v] = [latest Lambda^new_v < 0], initially [L_v < 0].
+    const bool window = stop == 2;
+    std::vector<uint8_t> pneg;
+    long long win = 0;
+    if (window) {
+      pneg.resize(N);
+      for (int v = 0; v < N; ++v) pneg[v] = L[v] < T(0);
+      Lam.assign(L, L + N);
+    }
     bool done = false;
     for (int t = 1; t <= max_iter && !done; ++t) {
-      for (int m = 0; m < M; ++m) {    // sequential order of check-nodes
+      for (int m = 0; m < M && !done; ++m) {  // sequential order of check-nodes
         T Sacc = T(0);
         int sig = 0;
+        bool flip = false;
         for (int e = g.cptr[m]; e < g.cptr[m + 1]; ++e) {
           const int v = g.cvar[e];
           T Rn = T(0);
@@ -237,6 +257,12 @@ struct Frame {
           T qn = lam - R[e];
           cnt[C_V2C] += 1;
           cnt[C_SUMS] += 2;
+          if (window) {                // Eq. (s4e24): sign flip of the posterior?
+            const uint8_t neg = lam < T(0);
+            flip |= neg != pneg[v];
+            pneg[v] = neg;
+            Lam[v] = lam;
+          }
           // d) C2B, Eq. (s4e21) in the S-domain
           T ph = phi_t(std::fabs(qn));
           Sacc = Sacc + ph;
@@ -250,6 +276,28 @@ struct Frame {
         }
         S[m] = Sacc;                   // Eq. (s4e23)
         sg[m] = static_cast<uint8_t>(sig);
+        if (window) {
+          win = (sig == 0 && !flip) ? win + 1 : 0;
+          if (win >= M) {              // success, Step 3: x_hat of the latest V2C phase
+            for (int v = 0; v < N; ++v) hard[v] = pneg[v];
+            if (soft) std::copy(Lam.begin(), Lam.end(), soft);
+            cnt[C_SWEEPS] += 1;
+            iters = t;
+            done = true;
+          }
+        }
+      }
+      if (window) {
+        if (!done && t == max_iter) {
+          for (int v = 0; v < N; ++v) hard[v] = pneg[v];
+          if (soft) std::copy(Lam.begin(), Lam.end(), soft);
+          cnt[C_SWEEPS] += 1;
+          iters = -t;
+          done = true;
+        } else if (!done) {
+          cnt[C_SWEEPS] += 1;
+        }
+        continue;
       }
       // flushed posterior and hard decision, Eqs. (s4e20), (s2e7)
       for (int v = 0; v < N; ++v) {
@@ -658,7 +706,8 @@ template <class T>
 int decode_batch(const Graph& g, int alg, const T* llr, int batch, int max_iter, int stop,
                  T alpha, uint8_t* hard, int32_t* iters, T* soft, uint8_t* flags,
                  int64_t* counts, int threads) {
-  if (batch < 0 || max_iter < 1 || (stop != 0 && stop != 1) || !llr || !hard || !iters)
+  if (batch < 0 || max_iter < 1 || stop < 0 || stop > 2 || (stop == 2 && alg != CBP_SP) ||
+      !llr || !hard || !iters)
     return -1;
   if (alg < 0 || alg > 5) return -1;
   if (alg == CBP_SP_OMEGA && sizeof(T) != sizeof(double)) return -1;

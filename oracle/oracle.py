@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liboracle.so")
 
 ALGS = {"cbp_sp": 0, "cbp_nms": 1, "lbp_nms": 2, "fbp_sp": 3, "lbp_sp": 4, "cbp_sp_omega": 5}
-STOPS = {"syndrome": 0, "none": 1}
+STOPS = {"syndrome": 0, "none": 1, "window": 2}
 COUNTERS = ("sweeps", "b2v", "v2c", "c2b", "sums", "products", "c2v", "flush")
 
 _lock = threading.Lock()
