@@ -70,7 +70,19 @@ typedef enum cbp_alg {
 
 typedef enum cbp_stop {
   CBP_STOP_SYNDROME = 0, /* stop a frame after the first sweep with H x^T = 0 */
-  CBP_STOP_NONE = 1      /* always run max_iter sweeps */
+  CBP_STOP_NONE = 1,     /* always run max_iter sweeps */
+  /* The paper's own rule, Step 2 (3) and Step 3 of Sec. IV-C (CBP_ALG_CBP_SP only): the
+   * decoding of a frame succeeds once M consecutive check updates (in the sequential
+   * order, counted across sweeps) each leave Omega_c > 0 (Eq. s4e2) and flip no sign of
+   * the posterior of Eq. (s4e20) against that variable's previous posterior (initially
+   * its channel LLR), Eq. (s4e24).  Decoding stops right after that update, possibly in
+   * the middle of a sweep; hard_out is the sign of each variable's latest Eq. (s4e20)
+   * posterior ("generated in the V2C phase"), iters the sweep in which the window
+   * filled (negated if it never did within max_iter sweeps).  No soft output; Z <= 384
+   * and base-row degree <= 32 (CBP_EUNSUPPORTED otherwise).  A variable of weight 1
+   * sends its channel LLR to its check in every sweep, so a wrong channel sign there
+   * keeps that check's Omega negative and the rule never fires. */
+  CBP_STOP_WINDOW = 2
 } cbp_stop;
 
 /* Options of cbp_decode_ex.  Zero-initialise, then set what you need;

@@ -18,7 +18,7 @@ import torch
 from . import build as _build
 
 ALGS = {"cbp_sp": 0, "cbp_nms": 1, "lbp_nms": 2, "fbp_sp": 3}
-STOPS = {"syndrome": 0, "none": 1}
+STOPS = {"syndrome": 0, "none": 1, "window": 2}
 STATUS = {0: "CBP_OK", -1: "CBP_EINVAL", -2: "CBP_ENOMEM", -3: "CBP_ECUDA",
           -4: "CBP_EUNSUPPORTED", -5: "CBP_EWORKSPACE", -6: "CBP_EDEVICE"}
 
@@ -140,7 +140,8 @@ class Code:
                lib().cbp_code_create(b.ctypes.data, b.shape[0], b.shape[1], self.Z, C.byref(h)))
         self._h = h
         n, m, k, e = C.c_int(), C.c_int(), C.c_int(), C.c_int()
-        _check("cbp_code_info", lib().cbp_code_info(h, C.byref(n), C.byref(m), C.byref(k), C.byref(e)))
+        _check("cbp_code_info",
+               lib().cbp_code_info(h, C.byref(n), C.byref(m), C.byref(k), C.byref(e)))
         self.N, self.M, self.K, self.E = n.value, m.value, k.value, e.value
         self.words = (self.N + 31) // 32
         self._ws = None
@@ -156,23 +157,24 @@ class Code:
             self._h = None
 
     # ------------------------------------------------------------------ workspace
-    def workspace_bytes(self, batch: int, alg: str = "cbp_sp") -> int:
+    def workspace_bytes(self, batch: int, alg: str = "cbp_sp", stop: str = "syndrome") -> int:
         nb = C.c_size_t()
-        o = _opts(alg, 0.75, "syndrome", None)
-        _check("cbp_workspace_bytes", lib().cbp_workspace_bytes(self._h, int(batch), C.byref(o), C.byref(nb)))
+        o = _opts(alg, 0.75, stop, None)
+        _check("cbp_workspace_bytes",
+               lib().cbp_workspace_bytes(self._h, int(batch), C.byref(o), C.byref(nb)))
         return nb.value
 
-    def workspace(self, batch: int, alg: str = "cbp_sp") -> torch.Tensor:
-        """A cached device workspace big enough for (batch, alg)."""
-        need = self.workspace_bytes(batch, alg)
+    def workspace(self, batch: int, alg: str = "cbp_sp", stop: str = "syndrome") -> torch.Tensor:
+        """A cached device workspace big enough for (batch, alg, stop)."""
+        need = self.workspace_bytes(batch, alg, stop)
         if self._ws is None or self._ws.numel() < need:
             self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=f"cuda:{self.device}")
         return self._ws
 
-    def launch_info(self, batch: int, alg: str = "cbp_sp") -> dict:
+    def launch_info(self, batch: int, alg: str = "cbp_sp", stop: str = "syndrome") -> dict:
         """The launch plan cbp_decode_ex would use (cbp_launch_info)."""
         info = (C.c_int * 8)()
-        o = _opts(alg, 0.75, "syndrome", None)
+        o = _opts(alg, 0.75, stop, None)
         _check("cbp_launch_info", lib().cbp_launch_info(self._h, int(batch), C.byref(o), info))
         keys = ("frames_per_sm", "threads_per_cta", "ctas_per_sm", "lane_groups_per_cta",
                 "frames_per_lane_group", "check_state_shared", "ctas", "team_lane_groups")
@@ -191,7 +193,7 @@ class Code:
             raise ValueError(f"llr must have {self.N} values per frame")
         if hard.numel() < B * self.words or iters.numel() < B:
             raise ValueError("output tensors too small")
-        ws = workspace if workspace is not None else self.workspace(B, alg)
+        ws = workspace if workspace is not None else self.workspace(B, alg, stop)
         o = _opts(alg, alpha, stop, soft.data_ptr() if soft is not None else None)
         rc = lib().cbp_decode_ex(self._h, llr.data_ptr(), hard.data_ptr(), iters.data_ptr(),
                                  int(max_iter), int(B), ws.data_ptr(), ws.numel(),

@@ -218,7 +218,8 @@ __global__ void __launch_bounds__(512) weighted_backward_kernel(const GParams p)
         const float gl = p.gsoft[frame * p.N + v];
         fr.gQ[v] = gl;
         gwx = gl * sgn * mag;
-        const float gd = gl * sgn * w * phi_deriv(fabsf(d), xlo, sh.tab) * (d < 0.0f ? -1.0f : 1.0f);
+        const float gd =
+            gl * sgn * w * phi_deriv(fabsf(d), xlo, sh.tab) * (d < 0.0f ? -1.0f : 1.0f);
         fr.gS[m] += gd;
         fr.gP[v] = -gd;
       }

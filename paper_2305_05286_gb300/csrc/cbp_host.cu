@@ -107,6 +107,8 @@ int device_init(int dev, DeviceInfo** out) {
     const Variant all[] = {{ALG_CBP_SP, true, 1},  {ALG_CBP_SP, false, 1},
                            {ALG_CBP_SP, true, 2},  {ALG_CBP_SP, false, 2},
                            {ALG_CBP_SP, true, 1, true}, {ALG_CBP_SP, false, 1, true},
+                           {ALG_CBP_SP, true, 1, false, true},
+                           {ALG_CBP_SP, false, 1, false, true},
                            {ALG_CBP_NMS, true, 1}, {ALG_CBP_NMS, false, 1},
                            {ALG_LBP_NMS, false, 1}, {ALG_FBP_SP, false, 1}};
     for (const Variant& v : all)
@@ -165,8 +167,10 @@ size_t shared_fixed_bytes(const Variant& v, const Shape& s, int groups) {
 size_t shared_frame_floats(const Variant& v, const Shape& s) {
   const size_t W = align4(s.words);
   switch (v.alg) {
-    case ALG_CBP_SP:
-      return v.fpt * (2 * static_cast<size_t>(s.ncomp) * s.Z + (v.chk_shared ? align4(s.M) : 0) + W);
+    case ALG_CBP_SP:  // WIN: + window counter/stop (4 ints) + one ok byte per check lane
+      return v.fpt * (2 * static_cast<size_t>(s.ncomp) * s.Z + (v.chk_shared ? align4(s.M) : 0) +
+                      W) +
+             (v.win ? 4 + align4((static_cast<size_t>(s.Z) + 3) / 4) : 0);
     case ALG_CBP_NMS:
       return align4(static_cast<size_t>(s.ncomp) * s.Z) +
              (v.chk_shared ? 2 * static_cast<size_t>((s.M + 1) & ~1) : 0) + W;
@@ -290,10 +294,16 @@ int team_groups_for(int Z, int groups) {
 // most resident frames per SM (ties: more resident warps); the variant with the most
 // resident frames wins (ties: the earlier one in the candidate list).  CBP_PLAN_CHK=0/1
 // and CBP_PLAN_FPT=1/2 in the environment restrict the candidates (tuning experiments).
-int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan* out) {
+int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan* out,
+              int stop = CBP_STOP_SYNDROME) {
   std::vector<Variant> cands;
   switch (alg) {
     case ALG_CBP_SP:
+      if (stop == CBP_STOP_WINDOW) {  // one frame per group, row degree <= 32 (flip masks)
+        if (c->Z > 384 || c->maxdeg > 32) return CBP_EUNSUPPORTED;
+        cands = {{ALG_CBP_SP, true, 1, false, true}, {ALG_CBP_SP, false, 1, false, true}};
+        break;
+      }
       cands = {{ALG_CBP_SP, true, 2}, {ALG_CBP_SP, false, 2}, {ALG_CBP_SP, true, 1},
                {ALG_CBP_SP, false, 1}};
       if (c->Z > 384) cands.push_back({ALG_CBP_SP, true, 1, true});
@@ -426,7 +436,11 @@ int check_opts(const cbp_opts_t* o, int* alg, float* alpha, int* stop, float** s
   *soft = nullptr;
   if (!o) return CBP_OK;
   if (o->alg < CBP_ALG_CBP_SP || o->alg > CBP_ALG_FBP_SP) return CBP_EINVAL;
-  if (o->stop_mode != CBP_STOP_SYNDROME && o->stop_mode != CBP_STOP_NONE) return CBP_EINVAL;
+  if (o->stop_mode != CBP_STOP_SYNDROME && o->stop_mode != CBP_STOP_NONE &&
+      o->stop_mode != CBP_STOP_WINDOW)
+    return CBP_EINVAL;
+  if (o->stop_mode == CBP_STOP_WINDOW && (o->alg != CBP_ALG_CBP_SP || o->soft_out))
+    return CBP_EINVAL;
   if (!std::isfinite(o->alpha)) return CBP_EINVAL;
   *alg = o->alg;
   if (o->alpha > 0.0f) *alpha = o->alpha;
@@ -604,7 +618,7 @@ int cbp_workspace_bytes(const cbp_code_t* c, int batch, const cbp_opts_t* opts, 
   if (int rc = current_device(&di, &dev)) return rc;
   if (dev != c->dev) return CBP_EDEVICE;
   Plan pl;
-  if (int rc = make_plan(c, *di, alg, batch, &pl)) return rc;
+  if (int rc = make_plan(c, *di, alg, batch, &pl, stop)) return rc;
   *bytes = pl.ws_bytes;
   return CBP_OK;
 }
@@ -620,7 +634,7 @@ int cbp_launch_info(const cbp_code_t* c, int batch, const cbp_opts_t* opts, int*
   if (int rc = current_device(&di, &dev)) return rc;
   if (dev != c->dev) return CBP_EDEVICE;
   Plan pl;
-  if (int rc = make_plan(c, *di, alg, batch, &pl)) return rc;
+  if (int rc = make_plan(c, *di, alg, batch, &pl, stop)) return rc;
   info[0] = pl.frames_per_sm;
   info[1] = pl.threads;
   info[2] = pl.ctas_per_sm;
@@ -650,7 +664,7 @@ int cbp_decode_ex(const cbp_code_t* c, const float* llr, uint32_t* hard_out, int
   if (int rc = current_device(&di, &dev)) return rc;
   if (dev != c->dev) return CBP_EDEVICE;
   Plan pl;
-  if (int rc = make_plan(c, *di, alg, batch, &pl)) return rc;
+  if (int rc = make_plan(c, *di, alg, batch, &pl, stop)) return rc;
   if (workspace_bytes < pl.ws_bytes) return CBP_EWORKSPACE;
 
   KParams p = code_params(c, *di, pl, batch, max_iter, stop, alpha);
@@ -712,7 +726,7 @@ int host_setup(const cbp_code* c, int chunk, const cbp_opts_t* opts, int* alg, f
   int dev = 0;
   if (int rc = current_device(dio, &dev)) return rc;
   if (dev != c->dev) return CBP_EDEVICE;
-  if (int rc = make_plan(c, **dio, *alg, chunk, pl)) return rc;
+  if (int rc = make_plan(c, **dio, *alg, chunk, pl, *stop)) return rc;
   *L = host_layout(c, chunk, pl->ws_bytes);
   return CBP_OK;
 }
@@ -847,7 +861,8 @@ int grad_setup(const cbp_code_t* c, int batch, int T, int ckpt, GParams* p, int*
   q.nseg = (T + ckpt - 1) / ckpt;
   q.F = F;
   q.frame_floats = static_cast<long long>(ff);
-  q.st_floats = static_cast<long long>((2 * static_cast<size_t>(c->N) + c->M + c->E + 3) & ~static_cast<size_t>(3));
+  q.st_floats = static_cast<long long>((2 * static_cast<size_t>(c->N) + c->M + c->E + 3) &
+                                       ~static_cast<size_t>(3));
   *p = q;
   if (dio) *dio = di;
   return CBP_OK;
@@ -1005,8 +1020,9 @@ int multi_plan_try(const cbp_multi_item_t* items, int n, int max_iter, int stop,
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return CBP_ECUDA;
   if (threads > fa.maxThreadsPerBlock) return CBP_EINVAL;
-  const long long budget_sm = di->smem_sm / ctas_target - 1024 - static_cast<long long>(fa.sharedSizeBytes);
-  const long long budget = std::min<long long>(budget_sm, di->smem_optin - static_cast<long long>(fa.sharedSizeBytes));
+  const long long stat = static_cast<long long>(fa.sharedSizeBytes);
+  const long long budget_sm = di->smem_sm / ctas_target - 1024 - stat;
+  const long long budget = std::min<long long>(budget_sm, di->smem_optin - stat);
   MultiPlan pl;
   pl.threads = threads;
   pl.fpt = fpt;

@@ -159,6 +159,7 @@ struct Variant {
   bool chk_shared;  // check state in shared memory (else in the workspace)
   int fpt = 1;      // frames per lane group (CBP-SP: 1 or 2, interleaved)
   bool wide = false;  // CBP-SP: instance that allows 1024 threads per CTA (Z > 512)
+  bool win = false;   // CBP-SP with the paper-literal stop (CBP_STOP_WINDOW)
 };
 
 // Sizes that fix the shared-memory and workspace layout of a launch.
@@ -181,6 +182,7 @@ cudaError_t decoder_set_smem(const Variant& v, int bytes);
 cudaError_t decoder_occupancy(const Variant& v, int threads, size_t smem, int* ctas);
 void* sp_kernel_ptr(bool chk_shared, int fpt, bool wide);  // cbp_sp.cu
 void* sp_multi_kernel_ptr(bool chk_shared, int fpt);        // cbp_sp.cu
+void* sp_win_kernel_ptr(bool chk_shared);                   // cbp_sp.cu
 cudaError_t launch_multi(bool chk_shared, int fpt, const MultiParams& mp, int grid, int threads,
                          size_t smem, cudaStream_t st);
 void* minsum_kernel_ptr(int alg, bool chk_shared);          // cbp_minsum.cu

@@ -58,15 +58,17 @@ struct Chunk {
   int qoff[CH];   // pair index of the variable in QP (weight >= 2) or SV (weight 1)
   int roff[CH];   // predecessor R slot (base entry of c_j, lane of c_j)
   uint32_t fl[CH];
+  int vidx[CH];   // variable index (paper-literal stop only)
 };
 
 // Loads of a chunk: (Q*, phi) of each variable, S of its predecessor check c_j, and
 // the edge's own R slot (read only once the frame is past its first sweep).
-template <int FPT, int CH>
+template <int FPT, int CH, bool WIN>
 __device__ __forceinline__ void load_chunk(Chunk<FPT, CH>& c, int kb, int k1,
                                            const SpEdge* __restrict__ s_spe, int z, int Z,
                                            bool later, const float* QP, const float* SV,
-                                           const float* S, const float* R) {
+                                           const float* S, const float* R,
+                                           const BaseEdge* __restrict__ g_edges) {
   using LV = Lanes<FPT>;
 #pragma unroll
   for (int j = 0; j < CH; ++j) {
@@ -85,6 +87,10 @@ __device__ __forceinline__ void load_chunk(Chunk<FPT, CH>& c, int kb, int k1,
         if (later) LV::ld(R, k * Z + z, c.ro[j]);
       }
       LV::ld(S, static_cast<int>(se.y) + z - uj, c.sj[j]);
+      if (WIN) {
+        const BaseEdge be = g_edges[k];
+        c.vidx[j] = be.c * Z + mod_add(z + be.s, Z);
+      }
     }
   }
 }
@@ -93,11 +99,15 @@ __device__ __forceinline__ void load_chunk(Chunk<FPT, CH>& c, int kb, int k1,
 // handled on the sign bits: no Q* is ever -0 (the channel LLRs are loaded as L + 0,
 // and a sum or difference of values that are not -0 is -0 only when both are -0 and
 // R^new is never -0), so the sign bit of Q* is [Q* < 0].
-template <int FPT, int CH>
+// WIN (paper-literal stop, one frame per group): the posterior Lambda = Q* + R^new of
+// Eq. (s4e20) is compared with the variable's previous one (sign bit in pbits); a flip
+// toggles the bit and is recorded in fmask (bit = edge position in the row).
+template <int FPT, int CH, bool WIN>
 __device__ __forceinline__ void update_chunk(const Chunk<FPT, CH>& c, int kb, int k1,
                                              const int* t, float* Sacc, uint32_t* sig,
                                              float xlo, const float4* __restrict__ tab,
-                                             float* QP, float* SV, float* R) {
+                                             float* QP, float* SV, float* R, uint32_t* pbits,
+                                             int k0, uint32_t& fmask) {
   using LV = Lanes<FPT>;
 #pragma unroll
   for (int j = 0; j < CH; ++j) {
@@ -119,7 +129,17 @@ __device__ __forceinline__ void update_chunk(const Chunk<FPT, CH>& c, int kb, in
         store_r |= !first;
         // V2C, Eqs. (s4e20), (s4e19); weight-1 column: c_j == c_i
         const float rold = self ? Rn[h] : (t[h] > 1 ? c.ro[j][h] : 0.0f);
-        qn[h] = __fsub_rn(__fadd_rn(c.q[j][h], Rn[h]), rold);
+        const float lam = __fadd_rn(c.q[j][h], Rn[h]);
+        qn[h] = __fsub_rn(lam, rold);
+        if (WIN) {  // Eq. (s4e24): did the posterior's sign flip?
+          const int v = c.vidx[j];
+          const uint32_t bit = 1u << (v & 31);
+          const bool neg = __float_as_uint(lam) >> 31;
+          if (neg != ((pbits[v >> 5] & bit) != 0)) {
+            atomicXor(pbits + (v >> 5), bit);
+            fmask |= 1u << (kb + j - k0);
+          }
+        }
         // C2B, Eq. (s4e21) as a sum of phi; the sign bits fold into sig
         phn[h] = phi_eval(fabsf(qn[h]), xlo, tab);
         Sacc[h] = __fadd_rn(Sacc[h], phn[h]);
@@ -139,30 +159,37 @@ __device__ __forceinline__ void update_chunk(const Chunk<FPT, CH>& c, int kb, in
 // current chunk's updates when DB (they never alias: a row reads its own R slots, the
 // beliefs of other rows and distinct variables, and writes predecessor R slots, its
 // variables and its own beliefs).
-template <int FPT, int CH, bool DB>
+template <int FPT, int CH, bool DB, bool WIN>
 __device__ __forceinline__ void row_edges(int k0, int k1, const SpEdge* __restrict__ s_spe,
                                           int z, int Z, bool later, const int* t, float* Sacc,
                                           uint32_t* sig, float xlo,
                                           const float4* __restrict__ tab, float* QP, float* SV,
-                                          const float* S, float* R) {
+                                          const float* S, float* R,
+                                          const BaseEdge* __restrict__ g_edges, uint32_t* pbits,
+                                          uint32_t& fmask) {
   if (DB) {
     Chunk<FPT, CH> A, B;
-    load_chunk<FPT, CH>(A, k0, k1, s_spe, z, Z, later, QP, SV, S, R);
+    load_chunk<FPT, CH, WIN>(A, k0, k1, s_spe, z, Z, later, QP, SV, S, R, g_edges);
     for (int kb = k0;;) {
-      if (kb + CH < k1) load_chunk<FPT, CH>(B, kb + CH, k1, s_spe, z, Z, later, QP, SV, S, R);
-      update_chunk<FPT, CH>(A, kb, k1, t, Sacc, sig, xlo, tab, QP, SV, R);
+      if (kb + CH < k1)
+        load_chunk<FPT, CH, WIN>(B, kb + CH, k1, s_spe, z, Z, later, QP, SV, S, R, g_edges);
+      update_chunk<FPT, CH, WIN>(A, kb, k1, t, Sacc, sig, xlo, tab, QP, SV, R, pbits, k0,
+                                 fmask);
       kb += CH;
       if (kb >= k1) break;
-      if (kb + CH < k1) load_chunk<FPT, CH>(A, kb + CH, k1, s_spe, z, Z, later, QP, SV, S, R);
-      update_chunk<FPT, CH>(B, kb, k1, t, Sacc, sig, xlo, tab, QP, SV, R);
+      if (kb + CH < k1)
+        load_chunk<FPT, CH, WIN>(A, kb + CH, k1, s_spe, z, Z, later, QP, SV, S, R, g_edges);
+      update_chunk<FPT, CH, WIN>(B, kb, k1, t, Sacc, sig, xlo, tab, QP, SV, R, pbits, k0,
+                                 fmask);
       kb += CH;
       if (kb >= k1) break;
     }
   } else {
     for (int kb = k0; kb < k1; kb += CH) {
       Chunk<FPT, CH> A;
-      load_chunk<FPT, CH>(A, kb, k1, s_spe, z, Z, later, QP, SV, S, R);
-      update_chunk<FPT, CH>(A, kb, k1, t, Sacc, sig, xlo, tab, QP, SV, R);
+      load_chunk<FPT, CH, WIN>(A, kb, k1, s_spe, z, Z, later, QP, SV, S, R, g_edges);
+      update_chunk<FPT, CH, WIN>(A, kb, k1, t, Sacc, sig, xlo, tab, QP, SV, R, pbits, k0,
+                                 fmask);
     }
   }
 }
@@ -179,17 +206,49 @@ __device__ __forceinline__ void prefetch_l2(const float* a, const float* b) {
                  : "memory");
 }
 
-// Step 2 of one sweep: the base rows in order, one team barrier after each.
-template <int FPT, int CH, bool DB>
+// Paper-literal stop: one thread of a lane group walks the row's check updates in order
+// (lane z = check r*Z + z) with the window counter wst[0]; wst[1] receives the lane at
+// which the counter reaches M, or -1.  ok[z] = 1 if check z left Omega > 0 and flipped
+// no posterior sign.
+__device__ __forceinline__ void window_scan(const unsigned char* ok, int Z, int M, int* wst) {
+  int run = wst[0], stop = -1, i = 0;
+  for (; i + 4 <= Z && stop < 0; i += 4) {
+    if (*reinterpret_cast<const uint32_t*>(ok + i) == 0x01010101u) {
+      if (run + 4 >= M) stop = i + (M - run - 1);
+      else run += 4;
+    } else {
+      for (int b = 0; b < 4 && stop < 0; ++b)
+        if (!ok[i + b]) run = 0;
+        else if (++run >= M) stop = i + b;
+    }
+  }
+  for (; i < Z && stop < 0; ++i)
+    if (!ok[i]) run = 0;
+    else if (++run >= M) stop = i;
+  wst[0] = stop < 0 ? run : M;
+  wst[1] = stop;
+}
+
+// Step 2 of one sweep: the base rows in order, one team barrier after each.  WIN adds
+// the window test of Eq. (s4e24) after every row (two more team barriers, executed by
+// every thread of the team); a group whose window fills stops in the middle of the row
+// at that check: lanes after it undo their posterior-sign updates, and `halted` keeps
+// the group idle for the rest of the sweep.
+template <int FPT, int CH, bool DB, bool WIN>
 __device__ __forceinline__ void sweep_rows(int mb, bool any, const int* s_rptr,
-                                        const SpEdge* __restrict__ s_spe, int z, int Z,
-                                        bool later, const int* t, float xlo,
-                                        const float4* __restrict__ tab, float* QP, float* SV,
-                                        float* S, float* R, int bar_id, int bar_n) {
+                                           const SpEdge* __restrict__ s_spe, int z, int Z,
+                                           bool later, const int* t, float xlo,
+                                           const float4* __restrict__ tab, float* QP, float* SV,
+                                           float* S, float* R, int bar_id, int bar_n,
+                                           const BaseEdge* __restrict__ g_edges,
+                                           uint32_t* pbits, int* wst, unsigned char* okb, int M,
+                                           bool& halted) {
   using LV = Lanes<FPT>;
   for (int r = 0; r < mb; ++r) {
-    if (any) {
-      const int k0 = s_rptr[r], k1 = s_rptr[r + 1];
+    const bool work = any && !(WIN && halted);
+    const int k0 = s_rptr[r], k1 = s_rptr[r + 1];
+    uint32_t fmask = 0, sig0 = 0;
+    if (work) {
       if (later && z == 0) {
         // the C2V slots of base row r + kPrefetchRows (cyclically) are contiguous in the
         // workspace: one bulk L2 prefetch per lane group brings them on chip while this
@@ -207,13 +266,30 @@ __device__ __forceinline__ void sweep_rows(int mb, bool any, const int* s_rptr,
         Sacc[h] = 0.0f;
         sig[h] = 0;
       }
-      row_edges<FPT, CH, DB>(k0, k1, s_spe, z, Z, later, t, Sacc, sig, xlo, tab, QP, SV,
-                                    S, R);
+      row_edges<FPT, CH, DB, WIN>(k0, k1, s_spe, z, Z, later, t, Sacc, sig, xlo, tab, QP, SV,
+                                  S, R, g_edges, pbits, fmask);
       float sv[FPT];
 #pragma unroll
       for (int h = 0; h < FPT; ++h)  // Sacc >= 0: its sign bit is free for sgn(Omega)
         sv[h] = __uint_as_float(__float_as_uint(Sacc[h]) | (sig[h] & 0x80000000u));
       LV::st(S, r * Z + z, sv);  // Eq. (s4e23); the sign bit carries sgn(Omega)
+      sig0 = sig[0];
+    }
+    if (WIN) {
+      if (work) okb[z] = ((sig0 & 0x80000000u) == 0 && fmask == 0) ? 1 : 0;  // Eq. (s4e2)
+      team_sync(bar_id, bar_n);
+      if (work && z == 0) window_scan(okb, Z, M, wst);
+      team_sync(bar_id, bar_n);
+      if (work && wst[1] >= 0) {
+        if (z > wst[1])  // checks after the stop point were not yet updated
+          for (int k = k0; k < k1; ++k)
+            if ((fmask >> (k - k0)) & 1u) {
+              const BaseEdge be = g_edges[k];
+              const int v = be.c * Z + mod_add(z + be.s, Z);
+              atomicXor(pbits + (v >> 5), 1u << (v & 31));
+            }
+        halted = true;
+      }
     }
     team_sync(bar_id, bar_n);
   }
@@ -222,9 +298,10 @@ __device__ __forceinline__ void sweep_rows(int mb, bool any, const int* s_rptr,
 // Decode frames frame0, frame0 + 1, ... of one code with the lane groups of this CTA:
 // frame slot k starts at frame0 + k and advances by `stride` when its frame stops, until
 // it passes `end`.  Returns when every slot of the CTA is idle.
-template <bool CHKS, int FPT, int CH, bool DB>
+template <bool CHKS, int FPT, int CH, bool DB, bool WIN = false>
 __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride, int end,
                                         unsigned char* smem, bool load_tab) {
+  static_assert(!WIN || FPT == 1, "the paper-literal stop runs one frame per lane group");
   using LV = Lanes<FPT>;
   const int Z = p.Z, N = p.N, M = p.M, words = p.words, G = p.F;
   const int tid = threadIdx.x;
@@ -278,6 +355,12 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
   }
   uint32_t* bits = reinterpret_cast<uint32_t*>(nxt);   // frame h: bits + h * wpad
   const int wpad = (words + 3) & ~3;
+  // WIN: bits hold [latest posterior < 0] per variable; then the window counter and stop
+  // lane (4 ints) and one ok byte per check lane
+  int* wst = reinterpret_cast<int*>(bits + FPT * wpad);
+  unsigned char* okb = reinterpret_cast<unsigned char*>(wst + 4);
+  if (WIN && lane)
+    for (int w = z; w < wpad; w += Z) bits[w] = 0u;
   SlotState* my = s_slot + (lane ? g : 0) * FPT;
   const float4* tab = s_tab;
   const float xlo = p.phi_xlo;
@@ -303,14 +386,16 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
         for (int c = 0; c < p.nb; ++c) {
           const uint2 ci = s_col[c];
           const int idx = ci.y & 0xffff;
-          if (ci.y & 0x10000u) {
-            const int s = int(ci.x >> 16);
-            SV[((idx * Z + z) * FPT + h) * 2] =
-                __fadd_rn(__ldg(src + c * Z + mod_add(z + s, Z)), 0.0f);  // -0 -> +0
-          } else {
-            QP[((idx * Z + z) * FPT + h) * 2] = __fadd_rn(__ldg(src + c * Z + z), 0.0f);
-          }
+          const int v =
+              (ci.y & 0x10000u) ? c * Z + mod_add(z + int(ci.x >> 16), Z) : c * Z + z;
+          const float L = __fadd_rn(__ldg(src + v), 0.0f);  // -0 -> +0
+          if (ci.y & 0x10000u)
+            SV[((idx * Z + z) * FPT + h) * 2] = L;
+          else
+            QP[((idx * Z + z) * FPT + h) * 2] = L;
+          if (WIN && L < 0.0f) atomicOr(bits + (v >> 5), 1u << (v & 31));
         }
+        if (WIN && z == 0) wst[0] = 0;
       }
     }
     if (!team_sync_or(bar_id, bar_n, any)) break;
@@ -319,114 +404,128 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
     bool later = false;  // some frame of the group is past its first sweep
 #pragma unroll
     for (int h = 0; h < FPT; ++h) later |= t[h] > 1;
-    sweep_rows<FPT, CH, DB>(p.mb, any, s_rptr, s_spe, z, Z, later, t, xlo, tab, QP, SV, S, R,
-                            bar_id, bar_n);
-
-    // ---- flushed posterior, hard decisions (Eq. s2e7)
-#pragma unroll
-    for (int h = 0; h < FPT; ++h)
-      if (act[h])
-        for (int w = z; w < words; w += Z) bits[h * wpad + w] = 0u;
-    if (lane && z == 0)
-#pragma unroll
-      for (int h = 0; h < FPT; ++h) my[h].unsat = 0;
-    team_sync(bar_id, bar_n);
-    for (int c = 0; c < p.nb; ++c) {
-      const uint2 ci = s_col[c];
-      const int idx = ci.y & 0xffff;
-      const int sk = int(ci.x >> 16), rk = int(ci.x & 0xffff);
-      float qv[FPT], pv[FPT], Sk[FPT];
-      int v = 0;
-      if (any) {
-        if (ci.y & 0x10000u) {  // weight-1 column: lane z owns its single check (rk, z)
-          LV::ld_pair(SV, idx * Z + z, qv, pv);
-          LV::ld(S, rk * Z + z, Sk);
-          v = c * Z + mod_add(z + sk, Z);
-        } else {
-          LV::ld_pair(QP, idx * Z + z, qv, pv);
-          int zk = z - sk;
-          zk = zk < 0 ? zk + Z : zk;
-          LV::ld(S, rk * Z + zk, Sk);
-          v = c * Z + z;
-        }
+    bool halted = false;
+    sweep_rows<FPT, CH, DB, WIN>(p.mb, any, s_rptr, s_spe, z, Z, later, t, xlo, tab, QP, SV, S,
+                                 R, bar_id, bar_n, p.edges, bits, wst, okb, M, halted);
+    bool done[FPT];
+    if constexpr (WIN) {
+      // Step 3: the hard decisions of the latest V2C phase; iters = the sweep in which
+      // the window filled, negated when it never did
+      done[0] = act[0] && (halted || t[0] >= p.max_iter);
+      if (done[0]) {
+        uint32_t* ho = p.hard + static_cast<long long>(frame[0]) * words;
+        for (int w = z; w < words; w += Z) ho[w] = bits[w];
+        if (z == 0) p.iters[frame[0]] = halted ? t[0] : -t[0];
       }
-#pragma unroll
-      for (int h = 0; h < FPT; ++h) {
-        bool neg = false;
-        if (act[h]) {
-          const float mag = phi_eval(fabsf(__fsub_rn(fabsf(Sk[h]), pv[h])), xlo, tab);
-          const float lb = __fadd_rn(
-              qv[h], __uint_as_float(__float_as_uint(mag) |
-                                     ((__float_as_uint(Sk[h]) ^ __float_as_uint(qv[h])) &
-                                      0x80000000u)));
-          neg = lb < 0.0f;
-          if (p.soft) p.soft[static_cast<long long>(frame[h]) * N + v] = lb;
-        }
-        if (words_aligned) {
-          // Z % 32 == 0: a warp lies inside one lane group, and its 32 variables of
-          // column c are 32 consecutive positions of the column (rotated by the shift
-          // for a weight-1 column), i.e. one aligned word or two partial ones
-          const unsigned wv = __ballot_sync(0xffffffffu, neg);
-          if ((tid & 31) == 0 && act[h]) {
-            uint32_t* wb = bits + h * wpad;
-            const int p0 = v - c * Z;  // position of this lane's variable in column c
-            const int sh = p0 & 31;
-            if (sh == 0) {
-              wb[v >> 5] = wv;  // the word holds exactly this warp's variables
-            } else {
-              atomicOr(wb + (v >> 5), wv << sh);
-              atomicOr(wb + ((c * Z + mod_add(p0 - sh + 32, Z)) >> 5), wv >> (32 - sh));
-            }
+      team_sync(bar_id, bar_n);
+      if (done[0])
+        for (int w = z; w < wpad; w += Z) bits[w] = 0u;  // ready for the slot's next frame
+    } else {
+      // ---- flushed posterior, hard decisions (Eq. s2e7)
+  #pragma unroll
+      for (int h = 0; h < FPT; ++h)
+        if (act[h])
+          for (int w = z; w < words; w += Z) bits[h * wpad + w] = 0u;
+      if (lane && z == 0)
+  #pragma unroll
+        for (int h = 0; h < FPT; ++h) my[h].unsat = 0;
+      team_sync(bar_id, bar_n);
+      for (int c = 0; c < p.nb; ++c) {
+        const uint2 ci = s_col[c];
+        const int idx = ci.y & 0xffff;
+        const int sk = int(ci.x >> 16), rk = int(ci.x & 0xffff);
+        float qv[FPT], pv[FPT], Sk[FPT];
+        int v = 0;
+        if (any) {
+          if (ci.y & 0x10000u) {  // weight-1 column: lane z owns its single check (rk, z)
+            LV::ld_pair(SV, idx * Z + z, qv, pv);
+            LV::ld(S, rk * Z + z, Sk);
+            v = c * Z + mod_add(z + sk, Z);
+          } else {
+            LV::ld_pair(QP, idx * Z + z, qv, pv);
+            int zk = z - sk;
+            zk = zk < 0 ? zk + Z : zk;
+            LV::ld(S, rk * Z + zk, Sk);
+            v = c * Z + z;
           }
-        } else {
-          warp_or_bit(bits + h * wpad + (v >> 5), neg ? (1u << (v & 31)) : 0u, act[h]);
         }
-      }
-    }
-    team_sync(bar_id, bar_n);
-    // ---- syndrome; a frame stops scanning once one of its checks is unsatisfied
-    if (any) {
-      bool open[FPT];
-      bool scan = false;
-#pragma unroll
-      for (int h = 0; h < FPT; ++h) {
-        open[h] = act[h];
-        scan |= open[h];
-      }
-      for (int r = 0; r < p.mb && scan; ++r) {
-        uint32_t pr[FPT];
-#pragma unroll
-        for (int h = 0; h < FPT; ++h) pr[h] = 0;
-        for (int k = s_rptr[r]; k < s_rptr[r + 1]; ++k) {
-          const BaseEdge be = p.edges[k];  // read through L1: the scan is off the hot path
-          const int v = be.c * Z + mod_add(z + be.s, Z);
-#pragma unroll
-          for (int h = 0; h < FPT; ++h) pr[h] ^= bits[h * wpad + (v >> 5)] >> (v & 31);
-        }
-        scan = false;
-#pragma unroll
+  #pragma unroll
         for (int h = 0; h < FPT; ++h) {
-          if (open[h] && (pr[h] & 1u)) my[h].unsat = 1;
-          open[h] = open[h] && !*static_cast<volatile int*>(&my[h].unsat);
+          bool neg = false;
+          if (act[h]) {
+            const float mag = phi_eval(fabsf(__fsub_rn(fabsf(Sk[h]), pv[h])), xlo, tab);
+            const float lb = __fadd_rn(
+                qv[h], __uint_as_float(__float_as_uint(mag) |
+                                       ((__float_as_uint(Sk[h]) ^ __float_as_uint(qv[h])) &
+                                        0x80000000u)));
+            neg = lb < 0.0f;
+            if (p.soft) p.soft[static_cast<long long>(frame[h]) * N + v] = lb;
+          }
+          if (words_aligned) {
+            // Z % 32 == 0: a warp lies inside one lane group, and its 32 variables of
+            // column c are 32 consecutive positions of the column (rotated by the shift
+            // for a weight-1 column), i.e. one aligned word or two partial ones
+            const unsigned wv = __ballot_sync(0xffffffffu, neg);
+            if ((tid & 31) == 0 && act[h]) {
+              uint32_t* wb = bits + h * wpad;
+              const int p0 = v - c * Z;  // position of this lane's variable in column c
+              const int sh = p0 & 31;
+              if (sh == 0) {
+                wb[v >> 5] = wv;  // the word holds exactly this warp's variables
+              } else {
+                atomicOr(wb + (v >> 5), wv << sh);
+                atomicOr(wb + ((c * Z + mod_add(p0 - sh + 32, Z)) >> 5), wv >> (32 - sh));
+              }
+            }
+          } else {
+            warp_or_bit(bits + h * wpad + (v >> 5), neg ? (1u << (v & 31)) : 0u, act[h]);
+          }
+        }
+      }
+      team_sync(bar_id, bar_n);
+      // ---- syndrome; a frame stops scanning once one of its checks is unsatisfied
+      if (any) {
+        bool open[FPT];
+        bool scan = false;
+  #pragma unroll
+        for (int h = 0; h < FPT; ++h) {
+          open[h] = act[h];
           scan |= open[h];
         }
-      }
-    }
-    team_sync(bar_id, bar_n);
-    bool done[FPT];
-#pragma unroll
-    for (int h = 0; h < FPT; ++h) {
-      done[h] = false;
-      if (act[h]) {
-        const bool ok = my[h].unsat == 0;
-        done[h] = (ok && p.stop == CBP_STOP_SYNDROME) || t[h] >= p.max_iter;
-        if (done[h]) {
-          uint32_t* ho = p.hard + static_cast<long long>(frame[h]) * words;
-          for (int w = z; w < words; w += Z) ho[w] = bits[h * wpad + w];
-          if (z == 0) p.iters[frame[h]] = ok ? t[h] : -t[h];
+        for (int r = 0; r < p.mb && scan; ++r) {
+          uint32_t pr[FPT];
+  #pragma unroll
+          for (int h = 0; h < FPT; ++h) pr[h] = 0;
+          for (int k = s_rptr[r]; k < s_rptr[r + 1]; ++k) {
+            const BaseEdge be = p.edges[k];  // read through L1: the scan is off the hot path
+            const int v = be.c * Z + mod_add(z + be.s, Z);
+  #pragma unroll
+            for (int h = 0; h < FPT; ++h) pr[h] ^= bits[h * wpad + (v >> 5)] >> (v & 31);
+          }
+          scan = false;
+  #pragma unroll
+          for (int h = 0; h < FPT; ++h) {
+            if (open[h] && (pr[h] & 1u)) my[h].unsat = 1;
+            open[h] = open[h] && !*static_cast<volatile int*>(&my[h].unsat);
+            scan |= open[h];
+          }
         }
       }
-    }
+      team_sync(bar_id, bar_n);
+  #pragma unroll
+      for (int h = 0; h < FPT; ++h) {
+        done[h] = false;
+        if (act[h]) {
+          const bool ok = my[h].unsat == 0;
+          done[h] = (ok && p.stop == CBP_STOP_SYNDROME) || t[h] >= p.max_iter;
+          if (done[h]) {
+            uint32_t* ho = p.hard + static_cast<long long>(frame[h]) * words;
+            for (int w = z; w < words; w += Z) ho[w] = bits[h * wpad + w];
+            if (z == 0) p.iters[frame[h]] = ok ? t[h] : -t[h];
+          }
+        }
+      }
+    }  // not WIN
     team_sync(bar_id, bar_n);
     if (z == 0) {
 #pragma unroll
@@ -448,6 +547,13 @@ template <bool CHKS, int FPT, int CH, bool DB, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) cbp_sp_kernel(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   sp_body<CHKS, FPT, CH, DB>(p, blockIdx.x * p.F * FPT, p.slots, p.batch, smem, true);
+}
+
+// The paper-literal stop of Eq. (s4e24) with the Step 3 output (one frame per group).
+template <bool CHKS>
+__global__ void __launch_bounds__(768, 1) cbp_sp_win_kernel(const KParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  sp_body<CHKS, 1, 4, false, true>(p, blockIdx.x * p.F, p.slots, p.batch, smem, true);
 }
 
 // Several codes in one persistent launch: each CTA takes chunks (code, frame range) from
@@ -486,6 +592,11 @@ void* sp_multi_kernel_ptr(bool chk_shared, int fpt) {
                       : reinterpret_cast<void*>(&cbp_sp_multi_kernel<false, 2, 4, true, 384>);
   return chk_shared ? reinterpret_cast<void*>(&cbp_sp_multi_kernel<true, 1, 4, false, 768>)
                     : reinterpret_cast<void*>(&cbp_sp_multi_kernel<false, 1, 4, false, 768>);
+}
+
+void* sp_win_kernel_ptr(bool chk_shared) {
+  return chk_shared ? reinterpret_cast<void*>(&cbp_sp_win_kernel<true>)
+                    : reinterpret_cast<void*>(&cbp_sp_win_kernel<false>);
 }
 
 void* sp_kernel_ptr(bool chk_shared, int fpt, bool wide) {

@@ -248,3 +248,41 @@ def test_min_sum_normalisations(code576, alpha):
     for alg in ("cbp_nms", "lbp_nms"):
         ref = oc.decode(fr.llr, alg=alg, max_iter=30, alpha=alpha, threads=THREADS)
         assert_parity(run_gpu(code, fr.llr, alg, alpha=alpha), ref, f"{alg} alpha {alpha}")
+
+
+@pytest.mark.parametrize("ebn0", [2.0, 3.0, 4.5])
+def test_paper_literal_window_stop(code576, ebn0):
+    qc, code, oc = code576
+    fr = I.make_frames(qc, 700, ebn0, seed=1300 + int(ebn0 * 10))
+    ref = oc.decode(fr.llr, alg="cbp_sp", max_iter=25, stop="window", threads=THREADS)
+    x = torch.from_numpy(fr.llr).cuda()
+    hard, iters, _ = code.decode(x, max_iter=25, alg="cbp_sp", stop="window")
+    torch.cuda.synchronize()
+    assert np.array_equal(iters.cpu().numpy(), ref["iters"])
+    assert np.array_equal(cbp.unpack_bits(hard, code.N).cpu().numpy(), ref["hard"])
+
+
+@pytest.mark.parametrize("Z", [1, 7, 32, 96])
+def test_paper_literal_window_stop_liftings(Z):
+    # Z = 1: one lane per group, many groups per team; 7: warps straddle groups; 32/96:
+    # whole warps; noiseless-ish frames make the window fill in the middle of rows
+    qc = I.relift(I.code_576(), Z)
+    code = cbp.Code.from_qc(qc)
+    oc = O.OracleCode(qc.base, qc.Z)
+    for ebn0, seed in ((3.5, 1), (6.0, 2)):
+        fr = I.make_frames(qc, 300, ebn0, seed=seed + Z)
+        ref = oc.decode(fr.llr, alg="cbp_sp", max_iter=15, stop="window", threads=THREADS)
+        hard, iters, _ = code.decode(torch.from_numpy(fr.llr).cuda(), max_iter=15, stop="window")
+        torch.cuda.synchronize()
+        assert np.array_equal(iters.cpu().numpy(), ref["iters"]), f"Z={Z} {ebn0} dB"
+        assert np.array_equal(cbp.unpack_bits(hard, code.N).cpu().numpy(), ref["hard"])
+
+
+def test_window_stop_option_checks(code576):
+    qc, code, _ = code576
+    x = torch.zeros((4, code.N), dtype=torch.float32, device="cuda")
+    for alg in ("cbp_nms", "lbp_nms", "fbp_sp"):
+        with pytest.raises(cbp.CbpError):
+            code.decode(x, max_iter=5, alg=alg, stop="window")
+    with pytest.raises(cbp.CbpError):   # no soft output in this mode
+        code.decode(x, max_iter=5, stop="window", soft=True)
