@@ -367,14 +367,16 @@ def run_sweep(args):
         llr, cw = I.make_frames_torch(qc, B, float(e), seed=2000 + i)
         hard = torch.empty((B, code.words), dtype=torch.int32, device="cuda")
         iters = torch.empty((B,), dtype=torch.int32, device="cuda")
-        for alg in ("cbp_sp", "cbp_nms", "lbp_nms", "fbp_sp"):
+        for alg in args.sweep_algs.split(","):
             ws = code.workspace(B, alg)
-            f = lambda: code.decode_into(llr, hard, iters, max_iter=MAX_ITER, alg=alg, workspace=ws)
+            f = lambda: code.decode_into(llr, hard, iters, max_iter=MAX_ITER, alg=alg,
+                                         alpha=args.alpha, workspace=ws)
             f()
             torch.cuda.synchronize()
             ms = timed_steps(torch, f, 1, stream)
             s = frame_stats(torch, cbp, qc, hard, iters, cw)
             row = {"ebn0_db": float(e), "alg": alg, "frames": B, "fer": s["fer"], "ber": s["ber"],
+                   "alpha": args.alpha if "nms" in alg else None,
                    "mean_iters": s["mean_iters"], "gbps": K * B / (ms / 1e3) / 1e9, "ms": ms}
             rows.append(row)
             print(json.dumps(row), flush=True)
@@ -595,6 +597,42 @@ def run_nms_study(args):
             del llr, cw
 
 
+def run_paper_rerun(args):
+    """The paper's own setting (Sec. V): rate-1/2 PEG codes of length 2048, regular (3,6)
+    and irregular, BPSK/AWGN, at most 200 iterations.  FER, BER and mean sweeps of CBP
+    (which equals layered BP bit for bit) with the syndrome stop and with the paper's
+    window stop, CBP min-sum (alpha = 1) and flooding BP.  The codes are general sparse
+    graphs, decoded as QC codes with Z = 1; frames are codewords of a GF(2) encoder."""
+    import torch
+
+    from paper_2305_05286_gb300 import cbp
+    from paper_2305_05286_gb300 import inputs as I
+
+    runs = [("cbp_sp", "syndrome"), ("cbp_sp", "window"), ("cbp_nms", "syndrome"),
+            ("fbp_sp", "syndrome")]
+    for name, qc in (("peg_3_6_n2048", I.code_peg_2048()),
+                     ("peg_irr_n2048", I.code_peg_irregular_2048())):
+        code = cbp.Code.from_qc(qc)
+        for pi, e in enumerate(np.arange(args.sweep_lo, args.sweep_hi + 1e-9, 0.25)):
+            fr = I.make_frames(qc, args.study_frames, float(e), seed=8000 + 10 * pi)
+            llr = torch.from_numpy(fr.llr).cuda()
+            cw = torch.from_numpy(fr.codewords).cuda()
+            for alg, stop in runs:
+                t0 = time.perf_counter()
+                hard, iters, _ = code.decode(llr, max_iter=200, alg=alg, alpha=1.0, stop=stop)
+                torch.cuda.synchronize()
+                secs = time.perf_counter() - t0
+                s = frame_stats(torch, cbp, qc, hard, iters, cw)
+                ok = iters > 0
+                print(json.dumps({
+                    "code": name, "ebn0_db": round(float(e), 2), "alg": alg, "stop": stop,
+                    "frames": args.study_frames, "fer": s["fer"], "ber": s["ber"],
+                    "mean_iters": s["mean_iters"],
+                    "mean_iters_stopped": float(iters[ok].abs().double().mean().item())
+                    if ok.any() else None,
+                    "stopped": float(ok.double().mean().item()), "seconds": secs}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -606,9 +644,13 @@ def main():
     ap.add_argument("--frames", type=int, default=FRAMES)
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--sweep-frames", type=int, default=16384)
+    ap.add_argument("--sweep-algs", default="cbp_sp,cbp_nms,lbp_nms,fbp_sp")
+    ap.add_argument("--alpha", type=float, default=0.75,
+                    help="min-sum normalisation for --sweep (the bench line uses 0.75)")
     ap.add_argument("--learned", action="store_true")
     ap.add_argument("--multi", action="store_true")
     ap.add_argument("--nms-study", action="store_true")
+    ap.add_argument("--paper-rerun", action="store_true")
     ap.add_argument("--study-frames", type=int, default=100000)
     ap.add_argument("--alphas", default="0.625,0.6875,0.75,0.8125,0.875,1.0")
     ap.add_argument("--train-steps", type=int, default=2000)
@@ -649,6 +691,8 @@ def main():
         run_multi_bench(args)
     elif args.nms_study:
         run_nms_study(args)
+    elif args.paper_rerun:
+        run_paper_rerun(args)
     else:
         run_ours(args, rank, world, dist)
     if dist:

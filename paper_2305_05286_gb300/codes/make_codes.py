@@ -29,6 +29,25 @@ def main():
                      "to two entries in the core rows 0-3.")
 
 
+# PEG codes of the paper's simulations (Sec. V): rate 1/2, N = 2048.
+PEG_IRREGULAR_LAMBDA = {2: 0.45, 3: 0.3708, 4: 0.0307, 12: 0.1485}
+
+
+def make_peg():
+    import numpy as np
+
+    rows = inputs.peg_graph(np.full(2048, 3), 1024, seed=5)
+    inputs.save_rows(os.path.join(HERE, "peg_3_6_n2048_seed5.txt"), rows, 2048,
+                     "Regular (3,6) PEG code, N=2048, M=1024 (rate 1/2), seed 5; "
+                     "one line of variable indices per check")
+    deg = inputs.peg_degrees(2048, PEG_IRREGULAR_LAMBDA)
+    rows = inputs.peg_graph(deg, 1024, seed=6)
+    inputs.save_rows(os.path.join(HERE, "peg_irr_n2048_seed6.txt"), rows, 2048,
+                     "Irregular PEG code, N=2048, M=1024, lambda(x) = 0.45x + 0.3708x^2 + "
+                     "0.0307x^3 + 0.1485x^11 (edge perspective), seed 6; "
+                     "one line of variable indices per check")
+
+
 # Mixed batch: eight codes of the same dual-diagonal structure, (Z, rate, mb x nb).
 MIXED = [(16, "1/3", 16, 24), (32, "2/5", 15, 25), (64, "1/2", 12, 24), (96, "2/3", 8, 24),
          (128, "3/4", 6, 24), (192, "5/6", 4, 24), (256, "8/9", 3, 27), (384, "1/2", 12, 24)]
@@ -50,3 +69,5 @@ def make_mixed():
 
 if __name__ == "__main__":
     main()
+    make_mixed()
+    make_peg()

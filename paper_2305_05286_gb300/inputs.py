@@ -272,6 +272,109 @@ def mixed_codes() -> list[QCCode]:
     return [load_code(n) for n in names]
 
 
+# ----------------------------------------------------------------------------
+# progressive edge growth (PEG) codes, the code family of the paper's Sec. V
+# ----------------------------------------------------------------------------
+def peg_graph(var_degrees, m: int, seed: int) -> list[list[int]]:
+    """Tanner graph by progressive edge growth (Hu, Eleftheriou and Arnold, IEEE Trans.
+    Inf. Theory 51(1), 2005).  Variables are placed in order of non-decreasing degree;
+    the first edge of a variable goes to a check of lowest current degree, every further
+    edge to a lowest-degree check among those farthest from the variable in the graph
+    built so far: the checks not reached by a breadth-first expansion from the
+    variable, taken at the depth where the reached set stops growing, or where it would
+    next cover every check.  Ties are broken by a seeded generator.  Returns the
+    variables of every check in ascending order."""
+    rng = np.random.default_rng(seed)
+    order = np.argsort(np.asarray(var_degrees), kind="stable")
+    n = len(var_degrees)
+    vc = [[] for _ in range(n)]        # checks of each variable
+    cv = [[] for _ in range(m)]        # variables of each check
+    deg = np.zeros(m, dtype=np.int64)
+
+    def pick(cands: np.ndarray) -> int:
+        d = deg[cands]
+        best = cands[d == d.min()]
+        return int(best[rng.integers(best.size)])
+
+    for v in order:
+        for k in range(int(var_degrees[v])):
+            if k == 0:
+                c = pick(np.arange(m))
+            else:
+                reached = np.zeros(m, dtype=bool)
+                seen_v = {int(v)}
+                front = [int(v)]
+                while True:
+                    new = {c for u in front for c in vc[u] if not reached[c]}
+                    if not new:                 # the reached set stopped growing
+                        cands = np.nonzero(~reached)[0]
+                        break
+                    if reached.sum() + len(new) == m:  # the next depth covers all checks
+                        cands = np.nonzero(~reached)[0]
+                        cands = np.array(sorted(set(cands.tolist()) & new), dtype=np.int64)
+                        break
+                    reached[list(new)] = True
+                    nxt = []
+                    for c in new:
+                        for u in cv[c]:
+                            if u not in seen_v:
+                                seen_v.add(u)
+                                nxt.append(u)
+                    front = nxt
+                c = pick(cands)
+            vc[v].append(c)
+            cv[c].append(int(v))
+            deg[c] += 1
+    return [sorted(r) for r in cv]
+
+
+def peg_degrees(n: int, lam: dict[int, float]) -> np.ndarray:
+    """Variable degrees for n variables from an edge-perspective distribution
+    lambda(x) = sum_i lam[i] x^(i-1): node fractions proportional to lam[i] / i, rounded
+    by largest remainder."""
+    w = np.array([lam[i] / i for i in sorted(lam)])
+    f = w / w.sum() * n
+    cnt = np.floor(f).astype(np.int64)
+    cnt[np.argsort(-(f - cnt))[: n - cnt.sum()]] += 1
+    return np.repeat(np.array(sorted(lam)), cnt)
+
+
+def code_from_rows(rows: list[list[int]], n: int, name: str = "") -> QCCode:
+    """A general sparse code as a QC code with Z = 1 (base entry 0 = a one of H)."""
+    base = np.full((len(rows), n), -1, dtype=np.int32)
+    for r, vs in enumerate(rows):
+        base[r, vs] = 0
+    return QCCode(base, 1, name)
+
+
+def save_rows(path: str, rows: list[list[int]], n: int, comment: str) -> None:
+    with open(path, "w") as f:
+        f.write(f"# {comment}\n")
+        f.write(f"{len(rows)} {n}\n")
+        for vs in rows:
+            f.write(" ".join(str(v) for v in vs) + "\n")
+
+
+def load_rows_code(name: str) -> QCCode:
+    """A code saved by save_rows (one line of variable indices per check)."""
+    with open(os.path.join(CODES_DIR, name + ".txt")) as f:
+        lines = [l for l in f if not l.startswith("#")]
+    m, n = (int(x) for x in lines[0].split())
+    rows = [[int(x) for x in l.split()] for l in lines[1: m + 1]]
+    return code_from_rows(rows, n, name)
+
+
+def code_peg_2048() -> QCCode:
+    """Regular (3,6) PEG code, N = 2048, rate 1/2 (seed 5)."""
+    return load_rows_code("peg_3_6_n2048_seed5")
+
+
+def code_peg_irregular_2048() -> QCCode:
+    """Irregular PEG code, N = 2048, rate 1/2, lambda(x) = 0.45x + 0.3708x^2 + 0.0307x^3
+    + 0.1485x^11 (seed 6)."""
+    return load_rows_code("peg_irr_n2048_seed6")
+
+
 def relift(code: QCCode, Z: int) -> QCCode:
     """Same base graph lifted by a smaller Z (shifts taken mod Z)."""
     b = code.base.copy()

@@ -286,3 +286,20 @@ def test_window_stop_option_checks(code576):
             code.decode(x, max_iter=5, alg=alg, stop="window")
     with pytest.raises(cbp.CbpError):   # no soft output in this mode
         code.decode(x, max_iter=5, stop="window", soft=True)
+
+
+@pytest.mark.parametrize("fn", [I.code_peg_2048, I.code_peg_irregular_2048])
+def test_peg_codes_all_decoders(fn):
+    # a general sparse code as Z = 1: one lane per group, 1024 base rows of degree ~6
+    qc = fn()
+    code = cbp.Code.from_qc(qc)
+    oc = O.OracleCode(qc.base, qc.Z)
+    fr = I.make_frames(qc, 96, 1.75, seed=77)
+    for alg, stop in (("cbp_sp", "syndrome"), ("cbp_sp", "window"), ("fbp_sp", "syndrome"),
+                      ("lbp_nms", "syndrome"), ("cbp_nms", "syndrome")):
+        ref = oc.decode(fr.llr, alg=alg, max_iter=40, stop=stop, alpha=1.0, threads=THREADS)
+        hard, iters, _ = code.decode(torch.from_numpy(fr.llr).cuda(), max_iter=40, alg=alg,
+                                     alpha=1.0, stop=stop)
+        torch.cuda.synchronize()
+        assert np.array_equal(iters.cpu().numpy(), ref["iters"]), f"{alg} {stop}"
+        assert np.array_equal(cbp.unpack_bits(hard, code.N).cpu().numpy(), ref["hard"])

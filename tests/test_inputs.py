@@ -88,3 +88,33 @@ def test_frames_are_reproducible():
     a = I.make_frames(c, 4, 1.5, seed=11)
     b = I.make_frames(c, 4, 1.5, seed=11)
     assert np.array_equal(a.llr, b.llr) and np.array_equal(a.codewords, b.codewords)
+
+
+@pytest.mark.parametrize("fn,seed,degrees", [
+    (I.code_peg_2048, 5, lambda: np.full(2048, 3)),
+    (I.code_peg_irregular_2048, 6,
+     lambda: I.peg_degrees(2048, {2: 0.45, 3: 0.3708, 4: 0.0307, 12: 0.1485})),
+])
+def test_peg_codes(fn, seed, degrees):
+    qc = fn()
+    assert qc.Z == 1 and qc.N == 2048 and qc.M == 1024
+    H = (qc.base >= 0).astype(np.int64)
+    want = np.asarray(degrees())
+    # every variable keeps its degree (the committed graph places them in degree order)
+    assert np.array_equal(np.sort(H.sum(0)), np.sort(want))
+    # PEG keeps the graph free of 4-cycles at this size: two checks share <= 1 variable
+    G = H @ H.T
+    np.fill_diagonal(G, 0)
+    assert G.max() <= 1
+    # the committed file is what the generator gives for the seed
+    rows = I.peg_graph(want, 1024, seed)
+    assert rows == [list(np.nonzero(H[r])[0]) for r in range(1024)]
+
+
+def test_peg_degrees_follow_the_edge_distribution():
+    lam = {2: 0.45, 3: 0.3708, 4: 0.0307, 12: 0.1485}
+    d = I.peg_degrees(2048, lam)
+    assert d.size == 2048
+    frac_edges = {i: (d == i).sum() * i / d.sum() for i in lam}
+    for i in lam:
+        assert abs(frac_edges[i] - lam[i]) < 0.003
