@@ -392,7 +392,8 @@ def run_learned(args):
     from paper_2305_05286_gb300 import cbp
     from paper_2305_05286_gb300 import inputs as I
 
-    qc = I.code_2304()
+    qc = {"2304": I.code_2304, "2304hb": I.code_2304_hb}[args.learned_code]()
+    zero = not I.is_lower_triangular(qc)  # all-zero codewords where the device encoder can't
     code = cbp.Code.from_qc(qc)
     K = (qc.nb - qc.mb) * qc.Z
     T, B = 10, args.train_frames
@@ -403,7 +404,7 @@ def run_learned(args):
     losses = []
     for step in range(args.train_steps):
         ebn0 = 1.0 + 2.0 * torch.rand(B, generator=g, device="cuda")
-        llr, cw = I.make_frames_torch(qc, B, ebn0, seed=5000 + step)
+        llr, cw = I.make_frames_torch(qc, B, ebn0, seed=5000 + step, zero_codeword=zero)
         soft = cbp.weighted_cbp(code, llr, w, T, 2)
         loss = torch.nn.functional.binary_cross_entropy_with_logits(-soft, cw.float())
         opt.zero_grad(set_to_none=True)
@@ -424,7 +425,8 @@ def run_learned(args):
         done = 0
         while done < args.eval_frames:
             n = min(chunk, args.eval_frames - done)
-            llr, cw = I.make_frames_torch(qc, n, e, seed=6000 + 1000 * pi + done // chunk)
+            llr, cw = I.make_frames_torch(qc, n, e, seed=6000 + 1000 * pi + done // chunk,
+                                          zero_codeword=zero)
             for name in stats:
                 ev0 = torch.cuda.Event(enable_timing=True)
                 ev1 = torch.cuda.Event(enable_timing=True)
@@ -450,7 +452,8 @@ def run_learned(args):
                    "sweeps": T if name != "cbp_stop" and name != "lbp_nms" else f"<= {T}"}
             rows.append(row)
             print(json.dumps(row), flush=True)
-    print(json.dumps({"learned_weights": wl.cpu().numpy().round(4).tolist(),
+    print(json.dumps({"code": args.learned_code, "zero_codeword": zero,
+                      "learned_weights": wl.cpu().numpy().round(4).tolist(),
                       "train_steps": args.train_steps, "train_frames": B,
                       "train_seconds": train_s, "loss_first_last": [losses[0], losses[-1]]}),
           flush=True)
@@ -654,6 +657,7 @@ def main():
     ap.add_argument("--study-frames", type=int, default=100000)
     ap.add_argument("--alphas", default="0.625,0.6875,0.75,0.8125,0.875,1.0")
     ap.add_argument("--train-steps", type=int, default=2000)
+    ap.add_argument("--learned-code", default="2304", choices=["2304", "2304hb"])
     ap.add_argument("--train-frames", type=int, default=8192)
     ap.add_argument("--eval-frames", type=int, default=1_000_000)
     ap.add_argument("--lr", type=float, default=0.01)

@@ -19,6 +19,11 @@ def main():
     b = inputs.make_dual_diagonal_code(mb=12, nb=24, Z=96, col_weight=3, seed=4)
     inputs.save_base(os.path.join(HERE, "qc_12x24_z96_seed4.txt"), b, 96,
                      "12x24 base, Z=96 (N=2304, rate 1/2), seed 4; same structure as the Z=24 code.")
+    b = inputs.make_dual_diagonal_code(mb=12, nb=24, Z=96, col_weight=3, seed=4, parity="hb")
+    inputs.save_base(os.path.join(HERE, "qc_12x24_z96_seed4_hb.txt"), b, 96,
+                     "12x24 base, Z=96 (N=2304, rate 1/2), seed 4, info columns by the same recipe.\n"
+                     "Parity columns 12-23 in the IEEE 802.16e form: column 12 has weight 3 (rows 0\n"
+                     "and 11 shift 1, row 6 shift 0), columns 13-23 hold rows j-1 and j (shift 0).")
     b = inputs.make_extension_code(mb=46, nb=68, kb=22, core=4, Z=384, density=0.25, seed=2)
     inputs.save_base(os.path.join(HERE, "qc_46x68_z384_seed2.txt"), b, 384,
                      "46x68 base, Z=384 (N=26112, K=8448, rate 22/68), seed 2.\n"

@@ -128,22 +128,35 @@ def _place(base, Z, r, c, rng, tries=200) -> bool:
     return False
 
 
-def make_dual_diagonal_code(mb: int, nb: int, Z: int, col_weight: int, seed: int) -> np.ndarray:
-    """Rate (nb-mb)/nb code: info columns of fixed weight + lower-bidiagonal parity.
+def make_dual_diagonal_code(mb: int, nb: int, Z: int, col_weight: int, seed: int,
+                            parity: str = "bidiagonal") -> np.ndarray:
+    """Rate (nb-mb)/nb code: info columns of fixed weight + a dual-diagonal parity part.
 
-    Parity column of row r is kb + r (shift 0) and row r >= 1 also holds column
-    kb + r - 1 (shift 0), so the last column has weight 1.  Info columns get
-    ``col_weight`` distinct random rows with shifts uniform in [0, Z), resampled
-    while they close a 4-cycle.  Draw order: info columns ascending, rows sorted.
+    parity="bidiagonal": parity column of row r is kb + r (shift 0) and row r >= 1 also
+    holds column kb + r - 1 (shift 0), so the last column has weight 1.
+    parity="hb": the IEEE 802.16e form -- the first parity column kb has weight 3 (rows
+    0 and mb - 1 with shift 1, row mb // 2 with shift 0) and columns kb + j, j >= 1, hold
+    rows j - 1 and j (shift 0): no parity column of weight 1.
+    Info columns get ``col_weight`` distinct random rows with shifts uniform in [0, Z),
+    resampled while they close a 4-cycle.  Draw order: info columns ascending, rows sorted.
     """
     rng = np.random.default_rng(seed)
     kb = nb - mb
     for _attempt in range(1000):
         base = -np.ones((mb, nb), dtype=np.int32)
-        for r in range(mb):
-            base[r, kb + r] = 0
-            if r >= 1:
-                base[r, kb + r - 1] = 0
+        if parity == "bidiagonal":
+            for r in range(mb):
+                base[r, kb + r] = 0
+                if r >= 1:
+                    base[r, kb + r - 1] = 0
+        elif parity == "hb":
+            base[0, kb] = base[mb - 1, kb] = 1 % Z
+            base[mb // 2, kb] = 0
+            for j in range(1, mb):
+                base[j - 1, kb + j] = 0
+                base[j, kb + j] = 0
+        else:
+            raise ValueError(parity)
         ok = True
         for c in range(kb):
             placed = False
@@ -258,6 +271,12 @@ def code_576() -> QCCode:
 def code_26112() -> QCCode:
     """46x68 base, Z=384, N=26112, rate 22/68 (the large-batch throughput workload)."""
     return load_code("qc_46x68_z384_seed2")
+
+
+def code_2304_hb() -> QCCode:
+    """12x24, Z=96 (N=2304, rate 1/2), seed 4, with the 802.16e parity part (no weight-1
+    column)."""
+    return load_code("qc_12x24_z96_seed4_hb")
 
 
 def code_2304() -> QCCode:
@@ -555,22 +574,29 @@ def make_frames(code: QCCode, frames: int, ebn0_db: float, seed: int,
     return Frames(llr=llr, codewords=cw, ebn0_db=ebn0_db, rate=rate)
 
 
-def make_frames_torch(code: QCCode, frames: int, ebn0_db, seed: int, device="cuda"):
+def make_frames_torch(code: QCCode, frames: int, ebn0_db, seed: int, device="cuda",
+                      zero_codeword: bool = False):
     """Device-generated frames (torch Philox generator), for large batches.
 
     Random info bits, block forward-substitution encoding, BPSK/AWGN.  ``ebn0_db``
-    is a float or a per-frame tensor.  Returns (llr float32 [F, N], codewords uint8).
+    is a float or a per-frame tensor.  ``zero_codeword`` sends the all-zero codeword
+    instead (any code; the decoders are symmetric under codeword sign flips, so error
+    statistics do not depend on the codeword).  Returns (llr float32 [F, N], codewords
+    uint8).
     """
     import torch
 
-    if not is_lower_triangular(code):
-        raise ValueError("device frame generation needs a block lower-triangular code")
     g = torch.Generator(device=device)
     g.manual_seed(seed)
     K = (code.nb - code.mb) * code.Z
     rate = K / code.N
-    info = torch.randint(0, 2, (frames, K), generator=g, device=device, dtype=torch.uint8)
-    cw = encode_lower_triangular_torch(code, info)
+    if zero_codeword:
+        cw = torch.zeros((frames, code.N), device=device, dtype=torch.uint8)
+    else:
+        if not is_lower_triangular(code):
+            raise ValueError("device encoding needs a block lower-triangular code")
+        info = torch.randint(0, 2, (frames, K), generator=g, device=device, dtype=torch.uint8)
+        cw = encode_lower_triangular_torch(code, info)
     noise = torch.randn((frames, code.N), generator=g, device=device, dtype=torch.float32)
     e = torch.as_tensor(ebn0_db, dtype=torch.float64, device=device)
     s2 = (1.0 / (2.0 * rate * torch.pow(10.0, e / 10.0))).to(torch.float32)

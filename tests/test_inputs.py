@@ -7,11 +7,12 @@ from paper_2305_05286_gb300 import inputs as I
 
 @pytest.mark.parametrize("fn,N,M,E,Z", [(I.code_576, 576, 288, 1416, 24),
                                          (I.code_2304, 2304, 1152, 5664, 96),
+                                         (I.code_2304_hb, 2304, 1152, 5856, 96),
                                          (I.code_26112, 26112, 17664, 141312, 384)])
 def test_committed_codes(fn, N, M, E, Z):
     c = fn()
     assert (c.N, c.M, c.E, c.Z) == (N, M, E, Z)
-    assert I.is_lower_triangular(c)
+    assert I.is_lower_triangular(c) == (fn is not I.code_2304_hb)
     assert ((c.base >= 0).sum(axis=1) >= 2).all()
     assert ((c.base >= 0).sum(axis=0) >= 1).all()
 
@@ -118,3 +119,13 @@ def test_peg_degrees_follow_the_edge_distribution():
     frac_edges = {i: (d == i).sum() * i / d.sum() for i in lam}
     for i in lam:
         assert abs(frac_edges[i] - lam[i]) < 0.003
+
+
+def test_802_16e_parity_part_has_no_weight_one_column():
+    qc = I.code_2304_hb()
+    w = (qc.base >= 0).sum(0)
+    assert w.min() >= 2 and w[12] == 3 and (w[13:] == 2).all()
+    # its parity part is invertible: H has full rank, so K = N - M
+    assert I.gf2_rank_dense(qc.dense_H()) == qc.M
+    fr = I.make_frames(qc, 4, 2.0, seed=1)
+    assert (qc.syndrome(fr.codewords) == 0).all()
