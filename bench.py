@@ -212,6 +212,22 @@ def workload_config(args, qc, note=None):
     return c
 
 
+def max_over_ranks(dist, ms: float) -> float:
+    """The slowest rank's time (the whole job waits for it); ms itself on one rank."""
+    if not dist:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def frame_seed(rank: int) -> int:
+    """Each replica decodes its own frames."""
+    return 2000 + 97 * rank
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -226,7 +242,7 @@ def run_ours(args, rank, world, dist):
     K = (qc.nb - qc.mb) * qc.Z
     code = cbp.Code.from_qc(qc)
     B = args.frames
-    llr, cw = I.make_frames_torch(qc, B, args.ebn0, seed=2000 + 97 * rank, device=dev)
+    llr, cw = I.make_frames_torch(qc, B, args.ebn0, seed=frame_seed(rank), device=dev)
     hard = torch.empty((B, code.words), dtype=torch.int32, device=dev)
     iters = torch.empty((B,), dtype=torch.int32, device=dev)
     ws = code.workspace(B, args.alg)
@@ -245,9 +261,7 @@ def run_ours(args, rank, world, dist):
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(dist, ms)
     st = frame_stats(torch, cbp, qc, hard, iters, cw)
     iters_dev = iters.cpu()  # for the end-to-end run's check (comparators reuse `iters`)
     value = world * K * B / (ms / 1e3) / 1e9
@@ -319,10 +333,7 @@ def run_ours(args, rank, world, dist):
         if dist:
             dist.barrier()
         ems = timed_steps(torch, e2e_step, args.steps, stream)
-        if dist:
-            t = torch.tensor([ems], dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(dist, ems)
         e2e = {"value": world * K * B / (ems / 1e3) / 1e9, "unit": "Gbit/s",
                "h2d_bytes_per_step": B * qc.N * 4,
                "d2h_bytes_per_step": B * code.words * 4 + B * 4, "ms_per_step": ems,
