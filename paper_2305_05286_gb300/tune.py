@@ -69,3 +69,39 @@ def tune_multi(codes, llrs, max_iter: int = 30, reps: int = 3, cands=None):
         raise RuntimeError("no launch option set fits these codes")
     table.sort(key=lambda t: t[0])
     return table[0][1], table
+
+
+# ----------------------------------------------------------------------------- cache
+_CACHE: dict = {}
+
+
+def cache_key(codes, batches) -> str:
+    """(GPU, codes, batch sizes rounded up to powers of two): launches that share a key
+    share their best options."""
+    import hashlib
+
+    h = hashlib.sha1()
+    h.update(torch.cuda.get_device_name().encode())
+    for c, b in zip(codes, batches):
+        h.update(c.base.tobytes())
+        h.update(f"{c.Z}:{1 << max(0, int(b) - 1).bit_length()};".encode())
+    return h.hexdigest()
+
+
+def tuned_options(codes, llrs, max_iter: int = 30, reps: int = 3, path: str | None = None):
+    """tune_multi once per cache key; later calls with the same key return the stored
+    options.  ``path`` (a JSON file) keeps the cache across processes."""
+    import json
+    import os
+
+    key = cache_key(codes, [x.shape[0] for x in llrs])
+    if path and not _CACHE and os.path.exists(path):
+        with open(path) as f:
+            _CACHE.update(json.load(f))
+    if key not in _CACHE:
+        best, _ = tune_multi(codes, llrs, max_iter, reps)
+        _CACHE[key] = best
+        if path:
+            with open(path, "w") as f:
+                json.dump(_CACHE, f, indent=1)
+    return dict(_CACHE[key])

@@ -187,3 +187,17 @@ def test_tuner_picks_a_valid_option_set(mixed):
         h1, i1 = run_single(c, a.cpu().numpy(), max_iter=10)
         assert np.array_equal(ii.cpu().numpy(), i1)
         assert np.array_equal(cbp.unpack_bits(hh, c.N).cpu().numpy(), h1)
+
+
+def test_tuner_cache(mixed, tmp_path):
+    qcs, codes = mixed
+    x = [torch.from_numpy(a).cuda() for a in frames_for(qcs, [64] * 8, seed=9300)]
+    path = str(tmp_path / "tune.json")
+    tune._CACHE.clear()
+    a = tune.tuned_options(codes, x, max_iter=5, reps=1, path=path)
+    tune._CACHE.clear()                      # a new process: read back from the file
+    b = tune.tuned_options(codes, x, max_iter=5, reps=1, path=path)
+    assert a == b and len(tune._CACHE) == 1
+    # batch sizes in the same power-of-two bucket share the entry
+    assert tune.cache_key(codes, [60] * 8) == tune.cache_key(codes, [64] * 8)
+    assert tune.cache_key(codes, [65] * 8) != tune.cache_key(codes, [64] * 8)
