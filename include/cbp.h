@@ -288,6 +288,15 @@ int cbp_decode_multi(const cbp_multi_item_t* items, int n_items, int max_iter,
  * on n device values: y[i] = phi(x[i]).  x, y device, 4-byte aligned, n >= 0. */
 int cbp_phi(const float* x, float* y, int64_t n, cbp_stream_t stream);
 
+/* Device status of a code handle.  Kernels never trap on bad input: they set a bit in
+ * the handle's status word and carry on (the frame's results are then undefined).
+ *   CBP_STATUS_NONFINITE_LLR  some decoded frame's channel LLRs held NaN or +-Inf
+ * cbp_device_status reads and clears the word in one atomic step on `stream`, waits for
+ * `stream`, and stores the flags in *flags (0 = no event since the last read).  It
+ * reports every decode with this handle that completed before the read, on any stream. */
+#define CBP_STATUS_NONFINITE_LLR 1u
+int cbp_device_status(const cbp_code_t* code, cbp_stream_t stream, uint32_t* flags);
+
 /* Measurement helper (no counterpart in the paper): the compute ceiling of the CBP-SP
  * edge update.  Launches `ctas` CTAs of 512 threads (ctas <= 0: every SM filled to its
  * occupancy limit) in which each thread runs `iters` rounds of 4 independent edge updates

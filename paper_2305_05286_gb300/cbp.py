@@ -28,7 +28,8 @@ EXPORTS = ("cbp_code_create", "cbp_code_destroy", "cbp_code_info", "cbp_workspac
            "cbp_decode_host", "cbp_grad_workspace_bytes",
            "cbp_decode_weighted", "cbp_decode_grad", "cbp_decode_noalloc",
            "cbp_multi_workspace_bytes", "cbp_multi_launch_info", "cbp_decode_multi", "cbp_phi",
-           "cbp_edge_ceiling", "cbp_strerror")
+           "cbp_edge_ceiling", "cbp_device_status", "cbp_strerror")
+STATUS_NONFINITE_LLR = 1
 MULTI_MAX_ITEMS = 8
 
 
@@ -101,6 +102,8 @@ def lib(build_if_needed: bool = True):
             L.cbp_decode_multi.argtypes = [MI, I, I, P, Z, P, MO]
             L.cbp_phi.restype = I
             L.cbp_phi.argtypes = [P, P, C.c_int64, P]
+            L.cbp_device_status.restype = I
+            L.cbp_device_status.argtypes = [P, P, C.POINTER(C.c_uint32)]
             L.cbp_edge_ceiling.restype = I
             L.cbp_edge_ceiling.argtypes = [I, I, P, Z, P, C.POINTER(C.c_int64), C.POINTER(I)]
             L.cbp_strerror.restype = C.c_char_p
@@ -155,6 +158,13 @@ class Code:
         if h is not None and h.value and _lib is not None:
             _lib.cbp_code_destroy(h)
             self._h = None
+
+    def device_status(self, stream=None) -> int:
+        """Read and clear the handle's device status word (cbp_device_status)."""
+        v = C.c_uint32()
+        _check("cbp_device_status",
+               lib().cbp_device_status(self._h, _stream_ptr(stream), C.byref(v)))
+        return v.value
 
     # ------------------------------------------------------------------ workspace
     def workspace_bytes(self, batch: int, alg: str = "cbp_sp", stop: str = "syndrome") -> int:

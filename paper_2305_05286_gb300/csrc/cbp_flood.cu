@@ -94,8 +94,14 @@ __global__ void __launch_bounds__(768, 1) flood_kernel(const KParams p) {
     const int frame = lane ? s_slot[f].frame : p.batch;
     const bool act = frame < p.batch;
     const float* L = p.llr + static_cast<long long>(act ? frame : 0) * N;
-    if (act && s_slot[f].t == 0)      // R = 0, so Lambda = L + 0 (Eq. s2e6)
-      for (int i = z; i < N; i += Z) lam[i] = __fadd_rn(__ldg(L + i), 0.0f);
+    if (act && s_slot[f].t == 0) {    // R = 0, so Lambda = L + 0 (Eq. s2e6)
+      bool bad = false;
+      for (int i = z; i < N; i += Z) {
+        lam[i] = __fadd_rn(__ldg(L + i), 0.0f);
+        bad |= non_finite(lam[i]);
+      }
+      if (bad) atomicOr(p.status, kStatusNonFiniteLlr);
+    }
     if (!__syncthreads_or(act)) break;
     const int t = act ? s_slot[f].t + 1 : 0;
 
@@ -177,6 +183,17 @@ __global__ void phi_kernel(const float* __restrict__ x, float* __restrict__ y, l
 }  // namespace
 
 void* flood_kernel_ptr() { return reinterpret_cast<void*>(&flood_kernel); }
+
+namespace {
+// Read and clear a code's status word in one atomic step: flags set by kernels still
+// running on other streams are either returned now or kept for the next read.
+__global__ void status_take_kernel(uint32_t* s) { s[1] = atomicExch(s, 0u); }
+}  // namespace
+
+cudaError_t launch_status_take(uint32_t* status, cudaStream_t st) {
+  status_take_kernel<<<1, 1, 0, st>>>(status);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_phi(const float* x, float* y, long long n, const float4* tab, float xlo,
                        cudaStream_t st) {

@@ -165,7 +165,12 @@ __global__ void __launch_bounds__(512) weighted_forward_kernel(const GParams p) 
   __syncthreads();
   if (act) {
     const float* L = p.llr + frame * p.N;
-    for (int i = z; i < p.N; i += Z) fr.Q[i] = L[i];  // Eq. (s4e15)
+    bool bad = false;
+    for (int i = z; i < p.N; i += Z) {
+      fr.Q[i] = L[i];  // Eq. (s4e15)
+      bad |= non_finite(L[i]);
+    }
+    if (bad) atomicOr(p.status, kStatusNonFiniteLlr);
   }
   for (int s = 0; s < p.nseg; ++s) {
     const int t0 = s * p.ckpt + 1, t1 = min(p.T, (s + 1) * p.ckpt);

@@ -395,6 +395,7 @@ int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan*
 KParams code_params(const cbp_code* c, const DeviceInfo& di, const Plan& pl, int batch,
                     int max_iter, int stop, float alpha) {
   KParams p{};
+  p.status = c->d.status;
   p.edges = c->d.edges;
   p.spe = c->d.spe;
   p.rptr = c->d.rptr;
@@ -557,7 +558,8 @@ int cbp_code_create(const int32_t* base, int mb, int nb, int Z, cbp_code_t** out
     spe[k].z = static_cast<uint32_t>(e.pe) * Z + d;
     spe[k].w = (static_cast<uint32_t>(Z) - sq) | ((static_cast<uint32_t>(Z) - d) << 16);
   }
-  bool ok = cudaMalloc(&c->d.edges, sizeof(BaseEdge) * edges.size()) == cudaSuccess &&
+  bool ok = cudaMalloc(&c->d.status, 2 * sizeof(uint32_t)) == cudaSuccess &&
+            cudaMalloc(&c->d.edges, sizeof(BaseEdge) * edges.size()) == cudaSuccess &&
             cudaMalloc(&c->d.spe, sizeof(SpEdge) * spe.size()) == cudaSuccess &&
             cudaMalloc(&c->d.rptr, sizeof(int) * rptr.size()) == cudaSuccess &&
             cudaMalloc(&c->d.cols, sizeof(ColEntry) * cols.size()) == cudaSuccess &&
@@ -566,7 +568,8 @@ int cbp_code_create(const int32_t* base, int mb, int nb, int Z, cbp_code_t** out
     cbp_code_destroy(c);
     return CBP_ENOMEM;
   }
-  ok = cudaMemcpy(c->d.edges, edges.data(), sizeof(BaseEdge) * edges.size(),
+  ok = cudaMemset(c->d.status, 0, 2 * sizeof(uint32_t)) == cudaSuccess &&
+       cudaMemcpy(c->d.edges, edges.data(), sizeof(BaseEdge) * edges.size(),
                   cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(c->d.spe, spe.data(), sizeof(SpEdge) * spe.size(), cudaMemcpyHostToDevice) ==
            cudaSuccess &&
@@ -586,6 +589,7 @@ int cbp_code_create(const int32_t* base, int mb, int nb, int Z, cbp_code_t** out
 
 void cbp_code_destroy(cbp_code_t* c) {
   if (!c) return;
+  cudaFree(c->d.status);
   cudaFree(c->d.edges);
   cudaFree(c->d.spe);
   cudaFree(c->d.rptr);
@@ -842,6 +846,7 @@ int grad_setup(const cbp_code_t* c, int batch, int T, int ckpt, GParams* p, int*
   *grid = static_cast<int>((static_cast<long long>(batch) + F - 1) / F);
   *smem = sm;
   GParams q{};
+  q.status = c->d.status;
   q.edges = c->d.edges;
   q.rptr = c->d.rptr;
   q.cols = c->d.cols;
@@ -1181,6 +1186,22 @@ int cbp_phi(const float* x, float* y, int64_t n, cbp_stream_t stream) {
                  cudaSuccess
              ? CBP_OK
              : CBP_ECUDA;
+}
+
+int cbp_device_status(const cbp_code_t* c, cbp_stream_t stream, uint32_t* flags) {
+  if (!c || !flags) return CBP_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CBP_ECUDA;
+  if (dev != c->dev) return CBP_EDEVICE;
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint32_t v = 0;
+  if (launch_status_take(c->d.status, st) != cudaSuccess ||
+      cudaMemcpyAsync(&v, c->d.status + 1, sizeof v, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return CBP_ECUDA;
+  *flags = v;
+  return CBP_OK;
 }
 
 int cbp_edge_ceiling(int ctas, int iters, float* sink, size_t sink_floats, cbp_stream_t stream,

@@ -104,7 +104,16 @@ struct ColEntry {
 using SpEdge = uint4;
 constexpr uint32_t kSpFirst = 1u << 30, kSpSelf = 1u << 31, kSpMask = kSpFirst - 1;
 
+// Device status word of a code handle (cbp_device_status): bits the kernels set instead of
+// trapping when an input breaks the ABI's contract.
+constexpr uint32_t kStatusNonFiniteLlr = 1u;  // a frame's channel LLRs hold NaN or +-Inf
+
+__device__ __forceinline__ bool non_finite(float x) {
+  return (__float_as_uint(x) & 0x7f800000u) == 0x7f800000u;
+}
+
 struct CodeDev {
+  uint32_t* status = nullptr;  // [2]: live flags, last value taken by cbp_device_status
   BaseEdge* edges = nullptr;  // [nnzb]
   SpEdge* spe = nullptr;      // [nnzb], CBP-SP kernel records
   int* rptr = nullptr;        // [mb + 1]
@@ -115,6 +124,7 @@ struct CodeDev {
 // Kernel parameters (passed by value).
 struct KParams {
   const float* llr;
+  uint32_t* status;      // the code's device status word
   uint32_t* hard;
   int32_t* iters;
   float* soft;
@@ -189,6 +199,7 @@ void* minsum_kernel_ptr(int alg, bool chk_shared);          // cbp_minsum.cu
 void* flood_kernel_ptr();              // cbp_flood.cu
 cudaError_t launch_phi(const float* x, float* y, long long n, const float4* tab, float xlo,
                        cudaStream_t st);
+cudaError_t launch_status_take(uint32_t* status, cudaStream_t st);  // cbp_flood.cu
 // CBP-SP edge-update ceiling (cbp_ceiling.cu): 512 threads per CTA.
 cudaError_t launch_edge_ceiling(const float4* tab, float xlo, int blocks, int iters,
                                 float* sink, cudaStream_t st, long long* edges);
@@ -197,6 +208,7 @@ int edge_ceiling_ctas_per_sm(int* ctas);
 // Weighted CBP (differentiable decoder), cbp_grad.cu.
 struct GParams {
   const float* llr;
+  uint32_t* status;      // the code's device status word
   const float* w;        // [T][mb]
   float* soft;           // forward output [batch][N]
   const float* gsoft;    // backward input [batch][N]

@@ -153,12 +153,17 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
     const bool act = frame < p.batch;
     if (act && my->t == 0) {  // Q*_v = L_v (CBP, Eq. s4e15); Lambda_v = L_v (LBP)
       const float* src = p.llr + static_cast<long long>(frame) * N;
+      bool bad = false;
       for (int c = 0; c < p.nb; ++c) {
         const uint2 ci = s_col[c];
         const int idx = ci.y & 0xffff;
-        if (ci.y & 0x10000u) SV[idx * Z + z] = __ldg(src + c * Z + mod_add(z + int(ci.x >> 16), Z));
-        else VAR[idx * Z + z] = __ldg(src + c * Z + z);
+        const float L =
+            __ldg(src + c * Z + ((ci.y & 0x10000u) ? mod_add(z + int(ci.x >> 16), Z) : z));
+        bad |= non_finite(L);
+        if (ci.y & 0x10000u) SV[idx * Z + z] = L;
+        else VAR[idx * Z + z] = L;
       }
+      if (bad) atomicOr(p.status, kStatusNonFiniteLlr);
     }
     if (!team_sync_or(bar_id, bar_n, act)) break;
     const int t = act ? my->t + 1 : 0;

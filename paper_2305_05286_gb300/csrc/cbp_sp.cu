@@ -383,12 +383,14 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
       any |= act[h];
       if (act[h] && my[h].t == 0) {  // Step 1, Eq. (s4e15): Q*_v = L_v for frame h
         const float* src = p.llr + static_cast<long long>(frame[h]) * N;
+        bool bad = false;
         for (int c = 0; c < p.nb; ++c) {
           const uint2 ci = s_col[c];
           const int idx = ci.y & 0xffff;
           const int v =
               (ci.y & 0x10000u) ? c * Z + mod_add(z + int(ci.x >> 16), Z) : c * Z + z;
           const float L = __fadd_rn(__ldg(src + v), 0.0f);  // -0 -> +0
+          bad |= non_finite(L);
           if (ci.y & 0x10000u)
             SV[((idx * Z + z) * FPT + h) * 2] = L;
           else
@@ -396,6 +398,7 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
           if (WIN && L < 0.0f) atomicOr(bits + (v >> 5), 1u << (v & 31));
         }
         if (WIN && z == 0) wst[0] = 0;
+        if (bad) atomicOr(p.status, kStatusNonFiniteLlr);
       }
     }
     if (!team_sync_or(bar_id, bar_n, any)) break;

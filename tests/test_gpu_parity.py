@@ -303,3 +303,27 @@ def test_peg_codes_all_decoders(fn):
         torch.cuda.synchronize()
         assert np.array_equal(iters.cpu().numpy(), ref["iters"]), f"{alg} {stop}"
         assert np.array_equal(cbp.unpack_bits(hard, code.N).cpu().numpy(), ref["hard"])
+
+
+def test_device_status_reports_non_finite_llrs(code576):
+    qc, code, _ = code576
+    fr = I.make_frames(qc, 40, 2.0, seed=31)
+    assert code.device_status() == 0
+    clean = run_gpu(code, fr.llr, "cbp_sp")
+    assert code.device_status() == 0          # finite input: nothing to report
+    bad = fr.llr.copy()
+    bad[7, 100] = np.nan
+    bad[21, 3] = np.inf
+    for alg in ALGS:
+        got = run_gpu(code, bad, alg)
+        assert code.device_status() == cbp.STATUS_NONFINITE_LLR, alg
+        assert code.device_status() == 0      # read and cleared
+        if alg == "cbp_sp":                   # the other frames are not affected
+            keep = np.ones(40, bool)
+            keep[[7, 21]] = False
+            assert np.array_equal(got[1][keep], clean[1][keep])
+            assert np.array_equal(got[0][keep], clean[0][keep])
+    w = torch.ones((3, qc.mb), device="cuda")
+    cbp.weighted_cbp(code, torch.from_numpy(bad).cuda(), w, 3)
+    torch.cuda.synchronize()
+    assert code.device_status() == cbp.STATUS_NONFINITE_LLR
