@@ -27,7 +27,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "CBP decoded Gbit/s at fixed FER vs same-GPU layered min-sum; % of roofline"
 # Operating point: the Eb/N0 grid point (0.25 dB grid) at which layered normalized
-# min-sum (alpha = 0.75) first reaches FER <= 1e-2 on this code.
+# min-sum (alpha = 0.75) first reaches FER <= 1e-2 on this code (measured with --sweep:
+# FER 0.25 at 2.25 dB, 9.8e-4 at 2.5 dB).
 EBN0_OPERATING = 2.5
 FRAMES = 65536
 MAX_ITER = 20
@@ -35,7 +36,12 @@ MAX_ITER = 20
 # Algorithmic issue slots per unit: the minimal instruction mix (FP32/INT32 arithmetic
 # and the memory instructions) of one edge update of one sweep, of the syndrome work
 # per edge and of the end-of-sweep posterior per variable, for each algorithm as
-# defined (phi evaluation: 21).  Derivation in the design doc.
+# defined.  phi: 20 (clamp 2, centre rounding 2, offset 1, k and offset above 2: 3,
+# regime test and selects 3, index 3, table fetch 2, Horner 3).  CBP-SP edge: 64 = B2V
+# 23 (|S| - phi 1, phi 20, sign 2) + V2C 2 + C2B 22 (phi 20, S add 1, sign 1) + memory 5
+# (Q*/phi load and store, S load, R load and store) + lane indexing 12.  Posterior per
+# variable 30 (loads, phi, sign, add, compare, packing).  Min-sum: compare/select chains
+# in place of phi.
 OPS_EDGE = {"cbp_sp": 64, "cbp_nms": 31, "lbp_nms": 28, "fbp_sp": 64}
 OPS_VAR = {"cbp_sp": 30, "cbp_nms": 10, "lbp_nms": 3, "fbp_sp": 5}
 OPS_SYN = 4
