@@ -268,3 +268,23 @@ def test_threads_do_not_change_results(c576, frames576):
     for k in ("hard", "iters", "soft"):
         assert np.array_equal(a[k], b[k])
     assert a["counts"] == b["counts"]
+
+
+@pytest.mark.parametrize("alg", ["cbp_sp", "fbp_sp"])
+def test_noiseless_posteriors_grow_until_saturation(c576, alg):
+    # with every channel LLR of the right sign, every message keeps that sign and the
+    # update maps are increasing in the incoming magnitudes: starting from R = 0, the
+    # posterior magnitudes can only grow from sweep to sweep (until phi saturates)
+    code, oc = c576
+    cw = np.zeros((2, code.N), np.uint8)
+    L = np.full((2, code.N), 1.5, np.float64)
+    L[1] = np.linspace(0.2, 3.0, code.N)
+    prev = None
+    for t in range(1, 7):
+        r = oc.decode(L, alg=alg, max_iter=t, stop="none", precision=64)
+        assert np.array_equal(r["hard"], cw)
+        mag = np.abs(r["soft"])
+        if prev is not None:
+            assert np.all(mag >= prev - 1e-12), f"sweep {t}"
+        prev = mag
+    assert prev.min() > 3.0
