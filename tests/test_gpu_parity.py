@@ -327,3 +327,34 @@ def test_device_status_reports_non_finite_llrs(code576):
     cbp.weighted_cbp(code, torch.from_numpy(bad).cuda(), w, 3)
     torch.cuda.synchronize()
     assert code.device_status() == cbp.STATUS_NONFINITE_LLR
+
+
+@pytest.mark.parametrize("chk,fpt", [("0", "1"), ("1", "1"), ("0", "2"), ("1", "2")])
+def test_every_cbp_sp_layout_variant(code576, monkeypatch, chk, fpt):
+    # the planner picks one variant per code; force each in turn (check state in shared
+    # memory or the workspace, one or two interleaved frames per lane group)
+    qc, code, oc = code576
+    monkeypatch.setenv("CBP_PLAN_CHK", chk)
+    monkeypatch.setenv("CBP_PLAN_FPT", fpt)
+    info = code.launch_info(777)
+    assert info["check_state_shared"] == int(chk) and info["frames_per_lane_group"] == int(fpt)
+    fr = I.make_frames(qc, 777, 2.0, seed=4000 + int(chk) * 10 + int(fpt))
+    for alg in ("cbp_sp", "cbp_nms"):
+        if alg == "cbp_nms" and fpt == "2":
+            continue                      # min-sum kernels run one frame per lane group
+        ref = oc.decode(fr.llr, alg=alg, max_iter=25, threads=THREADS)
+        assert_parity(run_gpu(code, fr.llr, alg, max_iter=25), ref, f"{alg} chk {chk} fpt {fpt}")
+
+
+@pytest.mark.parametrize("Z", [512, 1000])
+def test_lifts_above_384(Z):
+    # Z = 512: one lane group in a 768-thread CTA (idle lanes, one CTA-wide team);
+    # Z = 1000: only the 1024-thread instance fits, and Z is off the warp grid
+    qc = I.relift(I.code_576(), 24)
+    qc = I.QCCode(qc.base, Z)             # same shifts (all < 24), lifted by Z
+    code = cbp.Code.from_qc(qc)
+    oc = O.OracleCode(qc.base, qc.Z)
+    assert code.launch_info(40)["threads_per_cta"] > 384
+    fr = I.make_frames(qc, 40, 2.0, seed=Z)
+    ref = oc.decode(fr.llr, alg="cbp_sp", max_iter=20, threads=THREADS)
+    assert_parity(run_gpu(code, fr.llr, "cbp_sp", max_iter=20), ref, f"Z={Z}")
