@@ -1,4 +1,5 @@
-// Flooding sum-product BP (FBP) comparator on sm_103a, and the elementwise phi kernel.
+// Flooding sum-product BP (FBP) comparator on sm_103a, the elementwise phi kernel and the
+// one-thread kernel that reads and clears a code's device status word.
 //
 // Per iteration (Sec. II-A): every check computes its C2V messages from the V2C
 // messages Q_{v->c} = Lambda_v - R_{c->v} of the previous posterior (Eq. s3e1) with the

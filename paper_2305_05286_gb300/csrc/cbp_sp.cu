@@ -15,7 +15,15 @@
 //             not shared
 // A base row is processed in chunks of CH edges: the loads of a chunk are issued
 // together, then the CH edge updates run with independent phi evaluations, in
-// ascending column order (the order of the C2B fold).
+// ascending column order (the order of the C2B fold).  While a row runs, one thread per
+// group asks L2 for the next row's C2V block (a bulk prefetch, no data dependence).
+//
+// Kernels of this file, all on the same sweep body (sp_body):
+//   cbp_sp_kernel        one code, frames spread over persistent frame slots
+//   cbp_sp_win_kernel    the same with the paper's own stop, Eq. (s4e24), and the
+//                        Step 3 output (one frame per group, extra barriers per row)
+//   cbp_sp_multi_kernel  several codes in one launch: CTAs take (code, frame range)
+//                        chunks from a work counter
 #include "cbp_kernel_common.cuh"
 
 namespace cbp {

@@ -358,3 +358,43 @@ def test_lifts_above_384(Z):
     fr = I.make_frames(qc, 40, 2.0, seed=Z)
     ref = oc.decode(fr.llr, alg="cbp_sp", max_iter=20, threads=THREADS)
     assert_parity(run_gpu(code, fr.llr, "cbp_sp", max_iter=20), ref, f"Z={Z}")
+
+
+def test_concurrent_streams_and_host_threads(code576):
+    # the header's promise: calls with distinct outputs and workspaces may run concurrently
+    import threading
+
+    qc, code, _ = code576
+    frs = [I.make_frames(qc, 600, 2.0, seed=7000 + i).llr for i in range(4)]
+    ref = [run_gpu(code, a, "cbp_sp") for a in frs]
+    streams = [torch.cuda.Stream() for _ in frs]
+    xs = [torch.from_numpy(a).cuda() for a in frs]
+    outs = [(torch.empty((600, code.words), dtype=torch.int32, device="cuda"),
+             torch.empty((600,), dtype=torch.int32, device="cuda")) for _ in frs]
+    wss = [torch.empty(code.workspace_bytes(600), dtype=torch.uint8, device="cuda") for _ in frs]
+    torch.cuda.synchronize()
+
+    def work(i):
+        with torch.cuda.stream(streams[i]):
+            code.decode_into(xs[i], outs[i][0], outs[i][1], max_iter=30, workspace=wss[i],
+                             stream=streams[i])
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    torch.cuda.synchronize()
+    for (h, it), (rh, ri, _) in zip(outs, ref):
+        assert np.array_equal(it.cpu().numpy(), ri)
+        assert np.array_equal(cbp.unpack_bits(h, code.N).cpu().numpy(), rh)
+
+
+def test_decode_host_with_the_window_stop(code576):
+    qc, code, oc = code576
+    fr = I.make_frames(qc, 250, 3.0, seed=7100)
+    ref = oc.decode(fr.llr, alg="cbp_sp", max_iter=25, stop="window", threads=THREADS)
+    h, i = code.decode_host(torch.from_numpy(fr.llr).pin_memory(), max_iter=25, stop="window",
+                            chunk=64)
+    assert np.array_equal(i.numpy(), ref["iters"])
+    assert np.array_equal(cbp.unpack_bits(h, code.N).numpy(), ref["hard"])
