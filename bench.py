@@ -365,6 +365,12 @@ def run_ours(args, rank, world, dist):
             "roofline": roofline, "cpu_baseline": cpu, "comparators": comparators,
             "launch": code.launch_info(B, args.alg),
         }
+        if "lbp_nms" in comparators:  # the metric's comparison at the fixed-FER point
+            line["vs_layered_min_sum"] = {
+                "ratio": value / (world * comparators["lbp_nms"]["gbps"]),
+                "fer": st["fer"], "fer_layered_min_sum": comparators["lbp_nms"]["fer"],
+                "mean_sweeps": st["mean_iters"],
+                "mean_sweeps_layered_min_sum": comparators["lbp_nms"]["mean_iters"]}
         print(json.dumps(line), flush=True)
 
 
