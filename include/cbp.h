@@ -20,7 +20,7 @@
  * contraction into fused multiply-adds outside phi).  phi(x) = -log tanh(x/2)
  * (Eq. s2e5) is evaluated as phi(clamp(x, phi(30), 30)) by a cubic Taylor
  * expansion around the nearest point of a fixed grid (32 points per binade below
- * 2, 256 per binade from 2 to 30), coefficients from the closed-form derivatives of phi.
+ * 2, step 1/16 from 2 to 30), coefficients from the closed-form derivatives of phi.
  * The check-belief is stored as S_c = sum of phi(|Q|) with its sign (Appendix A,
  * Eqs. ae2-ae5).  A variable seen for the first time adds no C2V message; the C2V
  * store of Eq. (s4e22) writes the predecessor's slot R_{c_j->v}.

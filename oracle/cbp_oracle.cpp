@@ -45,7 +45,7 @@
 //     wins; B2V picks min2 when |Q*_v| equals min1; R = alpha * min with sign.
 //   * phi in FP32: phi(clamp(x, X_LO, X_HI)), X_HI = 30, X_LO = fl32(phi(30)),
 //     evaluated as a cubic Taylor polynomial around the nearest centre of a fixed
-//     grid (32 per binade below 2, 256 per binade from 2 to 30) with coefficients taken
+//     grid (32 per binade below 2, step 1/16 from 2 to 30) with coefficients taken
 //     from the closed-form derivatives of phi in FP64 and rounded to FP32.
 //     In FP64: phi(clamp(x, phi(50), 50)) from libm.
 #include <algorithm>
@@ -81,15 +81,13 @@ double phi64(double x) {
 inline uint32_t f2u(float f) { uint32_t u; std::memcpy(&u, &f, 4); return u; }
 inline float u2f(uint32_t u) { float f; std::memcpy(&f, &u, 4); return f; }
 
-// Grid of expansion centres: FP32 values with their low mantissa bits zero.  Below 2:
-// 18 zero bits (32 centres per binade), from 2^-43 (bit pattern 2688 << 18) to 2.0.
-// From 2 to 30: 15 zero bits (256 centres per binade, spacing 2^-7 .. 2^-4).  The
-// nearest centre rounds the bit pattern half up.
+// Grid of expansion centres.  Below 2: the FP32 values whose low 18 mantissa bits
+// are zero (32 centres per binade), from 2^-43 (bit pattern 2688 << 18) to 2.0.
+// From 2 to 30: k/16 for k = 32..480.
 constexpr int kLogBase = 2688;       // (bits of 2^-43) >> 18
 constexpr int kLogCount = 1409;      // centres 2^-43 ... 2.0
-constexpr uint32_t kHiBase = 0x8000; // (bits of 2.0) >> 15
-constexpr int kHiCount = 993;        // centres 2.0 ... 30.0
-constexpr int kSegments = kLogCount + kHiCount;
+constexpr int kUniCount = 449;       // centres 2.0, 2.0625, ..., 30.0
+constexpr int kSegments = kLogCount + kUniCount;
 
 struct PhiTable {
   std::vector<float> c;  // 4 coefficients per centre: value, then scaled derivatives
@@ -102,10 +100,8 @@ struct PhiTable {
         int e = static_cast<int>((cb >> 23) & 0xffu) - 127;
         h = std::ldexp(1.0, e);           // t = (x - m) / 2^e
       } else {
-        uint32_t cb = (kHiBase + static_cast<uint32_t>(i - kLogCount)) << 15;
-        m = static_cast<double>(u2f(cb));
-        int e = static_cast<int>((cb >> 23) & 0xffu) - 127;
-        h = std::ldexp(1.0, e - 8);       // t = (x - m) / 2^(e-8), the grid spacing
+        m = (32 + (i - kLogCount)) / 16.0;
+        h = 1.0 / 16.0;                   // t = (x - m) * 16
       }
       // phi(m), phi'(m) = -1/sinh m, phi''(m) = cosh m / sinh^2 m,
       // phi'''(m) = -(cosh^2 m + 1) / sinh^3 m; Taylor coefficients times h^k.
@@ -139,11 +135,10 @@ float phi32(float x) {
     float inv = u2f((254u - (cb >> 23)) << 23);       // 2^-e of the centre
     t = (x - m) * inv;
   } else {
-    uint32_t cb = (f2u(x) + 0x4000u) & 0xFFFF8000u;  // nearest centre
-    i = static_cast<int>(cb >> 15) - static_cast<int>(kHiBase) + kLogCount;
-    float m = u2f(cb);
-    float inv = u2f((262u - (cb >> 23)) << 23);       // 2^-(e-8) of the centre
-    t = (x - m) * inv;
+    float u = x * 16.0f;
+    float k = std::rint(u);
+    t = u - k;
+    i = static_cast<int>(k) - 32 + kLogCount;
   }
   const float* c = &phi_table().c[4 * i];
   float p = std::fma(c[3], t, c[2]);

@@ -16,28 +16,23 @@ namespace cbp {
 // Taylor coefficients phi^(k)(m) h^k / k! are computed in FP64 from
 //   phi(m) = log1p(2 / expm1(m)),  phi'(m) = -1/sinh m,  phi''(m) = cosh m / sinh^2 m,
 //   phi'''(m) = -(1 + cosh^2 m) / sinh^3 m,
-// and rounded to FP32.  Centres below 2: bit patterns (2688 + i) << 18, h = 2^e(m);
-// from 2 to 30: (0x8000 + j) << 15, h = 2^(e(m) - 8).
+// and rounded to FP32.
 // ---------------------------------------------------------------------------
-namespace {
-// centre of segment i and log2 of its normalisation h
-double phi_centre(int i, int* log2h) {
-  const uint32_t u = i < kPhiLogCount
-                         ? static_cast<uint32_t>(kPhiLogBase + i) << 18
-                         : static_cast<uint32_t>(kPhiHiBase + i - kPhiLogCount) << 15;
-  float mf;
-  std::memcpy(&mf, &u, sizeof mf);
-  const int e = static_cast<int>((u >> 23) & 0xffu) - 127;
-  *log2h = i < kPhiLogCount ? e : e - 8;
-  return mf;
-}
-}  // namespace
-
 void phi_table_host(float* coef, float* xlo) {
   for (int i = 0; i < kPhiSegments; ++i) {
-    int lh;
-    const double m = phi_centre(i, &lh);
-    const double h = std::ldexp(1.0, lh);
+    double m, h;
+    if (i < kPhiLogCount) {
+      uint32_t u = static_cast<uint32_t>(kPhiLogBase + i) << 18;
+      float mf;
+      std::memcpy(&mf, &u, sizeof mf);
+      m = mf;
+      int ex;
+      std::frexp(m, &ex);      // m = f * 2^ex, f in [0.5, 1)
+      h = std::ldexp(1.0, ex - 1);
+    } else {
+      m = static_cast<double>(i - kPhiLogCount + 32) / 16.0;
+      h = 0.0625;
+    }
     const double a = h / std::sinh(m);
     const double co = std::cosh(m);
     coef[4 * i + 0] = static_cast<float>(std::log1p(2.0 / std::expm1(m)));
@@ -48,13 +43,22 @@ void phi_table_host(float* coef, float* xlo) {
   *xlo = static_cast<float>(std::log1p(2.0 / std::expm1(30.0)));
 }
 
-// Coefficient k divided by h^k.  ldexp by a power of two is exact while the value stays
-// normal, which every coefficient does (the largest, |c3| / h^3 at m = 2^-43, is about
-// 2^127.4).
+// Coefficient k divided by h^k: h = 2^(e - 1) for a centre m = f 2^e (f in [0.5, 1)),
+// h = 1/16 above 2.  ldexp by a power of two is exact while the value stays normal,
+// which every coefficient does (the largest, |c3| / h^3 at m = 2^-43, is about 2^127.4).
 void phi_table_device_form(const float* coef, float* dev) {
   for (int i = 0; i < kPhiSegments; ++i) {
-    int lh;
-    phi_centre(i, &lh);
+    int lh;  // log2 h
+    if (i < kPhiLogCount) {
+      uint32_t u = static_cast<uint32_t>(kPhiLogBase + i) << 18;
+      float mf;
+      std::memcpy(&mf, &u, sizeof mf);
+      int ex;
+      std::frexp(static_cast<double>(mf), &ex);
+      lh = ex - 1;
+    } else {
+      lh = -4;
+    }
     for (int k = 0; k < 4; ++k) dev[4 * i + k] = std::ldexp(coef[4 * i + k], -k * lh);
   }
 }

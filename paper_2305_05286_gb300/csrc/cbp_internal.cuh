@@ -13,43 +13,39 @@ namespace cbp {
 // ----------------------------------------------------------------------------
 // phi(x) = -log tanh(x/2), Eq. (s2e5), in FP32.
 // phi(clamp(x, X_LO, 30)) with X_LO = fl32(phi(30)); cubic Taylor polynomial around
-// the nearest grid centre.  The centres are FP32 values with their low mantissa bits
-// zero: 18 bits below 2 (bit patterns (2688 + i) << 18, 2^-43 .. 2.0, 32 per binade),
-// 15 bits from 2 to 30 ((0x8000 + j) << 15, 256 per binade); the nearest centre rounds
-// the bit pattern half up.  Local variable t = (x - centre) / h, h = 2^e(centre) below
-// 2 and 2^(e(centre) - 8) (the spacing) above; coefficients phi^(k)(m) h^k / k! rounded
-// to FP32.  The device table holds them divided by h^k (exact: h is a power of two and
-// no value leaves the normal FP32 range), so the kernels run the same Horner steps on
-// d = x - centre (exact by Sterbenz) without forming t; every rounding is the scaled
-// one times a power of two, so the result is bit-identical to the t form.  One code
-// path serves both regimes: only the number of rounded bits and the index offset
-// differ.
+// the nearest grid centre: below 2 the FP32 values whose low 18 mantissa bits are
+// zero (bit patterns (2688 + i) << 18, i = 0..1408, i.e. 2^-43 .. 2.0), local variable
+// t = (x - centre) / h with h = 2^e(centre); from 2 to 30 the centres k/16, h = 1/16.
+// The coefficients are phi^(k)(m) h^k / k! rounded to FP32.  The device table holds
+// them divided by h^k (exact: h is a power of two and no value leaves the normal FP32
+// range), so the kernels evaluate the same Horner steps on d = x - centre (exact by
+// Sterbenz) without forming t; every rounding is the scaled one times a power of two,
+// so the result is bit-identical to the t form.
 // ----------------------------------------------------------------------------
 constexpr int kPhiLogBase = 2688;
 constexpr int kPhiLogCount = 1409;
-constexpr int kPhiHiBase = 0x8000;   // (bits of 2.0) >> 15
-constexpr int kPhiHiCount = 993;     // centres 2.0 .. 30.0
-constexpr int kPhiSegments = kPhiLogCount + kPhiHiCount;
+constexpr int kPhiSegments = kPhiLogCount + 449;
 
 // Host: fill the coefficient table (4 floats per centre, the t form) and the lower clamp.
 void phi_table_host(float* coef, float* xlo);
 // Host: the device form of the table (coefficient k divided by h^k).
 void phi_table_device_form(const float* coef, float* dev);
 
-// Table index and offset d = x - centre of a clamped x (0 < x <= 30).
-__device__ __forceinline__ int phi_segment(float x, float* d) {
-  const uint32_t b = __float_as_uint(x);
-  const bool lo = b < 0x40000000u;           // x < 2
-  const uint32_t sh = lo ? 18u : 15u;
-  const uint32_t q = (b + (lo ? 0x20000u : 0x4000u)) >> sh;
-  *d = __fsub_rn(x, __uint_as_float(q << sh));
-  return static_cast<int>(q) + (lo ? -kPhiLogBase : kPhiLogCount - kPhiHiBase);
-}
-
 __device__ __forceinline__ float phi_eval(float x, float xlo, const float4* __restrict__ tab) {
   x = fminf(fmaxf(x, xlo), 30.0f);
-  float d;
-  const float4 c = tab[phi_segment(x, &d)];
+  // below 2: nearest centre cb (round the low 18 mantissa bits), d = x - cb
+  const uint32_t cb = (__float_as_uint(x) + 0x20000u) & 0xFFFC0000u;
+  const float dl = __fsub_rn(x, __uint_as_float(cb));
+  // 2 to 30: k = rint(16x) by adding 1.5 * 2^23 (16x is exact and below 2^22), d = x - k/16
+  constexpr float kMagic = 12582912.0f;
+  const float y = __fmaf_rn(x, 16.0f, kMagic);
+  const float du = __fmaf_rn(__fsub_rn(y, kMagic), -0.0625f, x);
+  const bool lo = x < 2.0f;
+  const float d = lo ? dl : du;
+  const int i = lo ? static_cast<int>(cb >> 18) - kPhiLogBase
+                   : static_cast<int>(__float_as_uint(y) - __float_as_uint(kMagic)) +
+                         (kPhiLogCount - 32);
+  const float4 c = tab[i];
   float p = __fmaf_rn(c.w, d, c.z);
   p = __fmaf_rn(p, d, c.y);
   return __fmaf_rn(p, d, c.x);
@@ -60,8 +56,17 @@ __device__ __forceinline__ float phi_eval(float x, float xlo, const float4* __re
 __device__ __forceinline__ float phi_deriv(float x, float xlo, const float4* __restrict__ tab) {
   const bool inside = x >= xlo && x <= 30.0f;
   x = fminf(fmaxf(x, xlo), 30.0f);
-  float d;
-  const float4 c = tab[phi_segment(x, &d)];
+  const uint32_t cb = (__float_as_uint(x) + 0x20000u) & 0xFFFC0000u;
+  const float dl = __fsub_rn(x, __uint_as_float(cb));
+  constexpr float kMagic = 12582912.0f;
+  const float y = __fmaf_rn(x, 16.0f, kMagic);
+  const float du = __fmaf_rn(__fsub_rn(y, kMagic), -0.0625f, x);
+  const bool lo = x < 2.0f;
+  const float d = lo ? dl : du;
+  const int i = lo ? static_cast<int>(cb >> 18) - kPhiLogBase
+                   : static_cast<int>(__float_as_uint(y) - __float_as_uint(kMagic)) +
+                         (kPhiLogCount - 32);
+  const float4 c = tab[i];
   const float dp = __fmaf_rn(__fmaf_rn(3.0f * c.w, d, 2.0f * c.z), d, c.y);
   return inside ? dp : 0.0f;
 }
