@@ -6,7 +6,8 @@ namespace cbp {
 static void* select_kernel(const Variant& v) {
   switch (v.alg) {
     case ALG_CBP_SP:
-      return v.win ? sp_win_kernel_ptr(v.chk_shared) : sp_kernel_ptr(v.chk_shared, v.fpt, v.wide);
+      return v.win ? sp_win_kernel_ptr(v.chk_shared)
+                   : sp_kernel_ptr(v.chk_shared, v.fpt, v.wide, v.self_last);
     case ALG_CBP_NMS:
     case ALG_LBP_NMS: return minsum_kernel_ptr(v.alg, v.chk_shared);
     case ALG_FBP_SP: return flood_kernel_ptr();

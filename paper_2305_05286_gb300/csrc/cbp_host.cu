@@ -109,6 +109,8 @@ int device_init(int dev, DeviceInfo** out) {
                            {ALG_CBP_SP, true, 1, true}, {ALG_CBP_SP, false, 1, true},
                            {ALG_CBP_SP, true, 1, false, true},
                            {ALG_CBP_SP, false, 1, false, true},
+                           {ALG_CBP_SP, true, 1, false, false, true},
+                           {ALG_CBP_SP, false, 1, false, false, true},
                            {ALG_CBP_NMS, true, 1}, {ALG_CBP_NMS, false, 1},
                            {ALG_LBP_NMS, false, 1}, {ALG_FBP_SP, false, 1}};
     for (const Variant& v : all)
@@ -220,6 +222,7 @@ struct cbp_code {
   int dev = 0;
   int mb = 0, nb = 0, Z = 0, N = 0, M = 0, E = 0, K = -1, nnzb = 0, maxdeg = 0;
   int ncomp = 0, nself = 0;  // columns of weight >= 2 / of weight 1
+  bool self_last = true;     // every row holds at most one weight-1 entry, as its last
   CodeDev d;
   Shape shape() const {
     return Shape{Z, N, M, E, nnzb, mb, nb, (N + 31) / 32, ncomp, nself};
@@ -304,8 +307,9 @@ int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan*
         cands = {{ALG_CBP_SP, true, 1, false, true}, {ALG_CBP_SP, false, 1, false, true}};
         break;
       }
-      cands = {{ALG_CBP_SP, true, 2}, {ALG_CBP_SP, false, 2}, {ALG_CBP_SP, true, 1},
-               {ALG_CBP_SP, false, 1}};
+      cands = {{ALG_CBP_SP, true, 2}, {ALG_CBP_SP, false, 2},
+               {ALG_CBP_SP, true, 1, false, false, c->self_last},
+               {ALG_CBP_SP, false, 1, false, false, c->self_last}};
       if (c->Z > 384) cands.push_back({ALG_CBP_SP, true, 1, true});
       if (c->Z > 384) cands.push_back({ALG_CBP_SP, false, 1, true});
       break;
@@ -523,6 +527,9 @@ int cbp_code_create(const int32_t* base, int mb, int nb, int Z, cbp_code_t** out
 
   cbp_code* c = new (std::nothrow) cbp_code;
   if (!c) return CBP_ENOMEM;
+  for (int r = 0; r < mb && c->self_last; ++r)
+    for (int k = rptr[r]; k < rptr[r + 1]; ++k)
+      if ((edges[k].flags & kSelf) && k != rptr[r + 1] - 1) c->self_last = false;
   c->dev = dev;
   c->mb = mb;
   c->nb = nb;

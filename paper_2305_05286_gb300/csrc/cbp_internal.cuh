@@ -170,6 +170,7 @@ struct Variant {
   int fpt = 1;      // frames per lane group (CBP-SP: 1 or 2, interleaved)
   bool wide = false;  // CBP-SP: instance that allows 1024 threads per CTA (Z > 512)
   bool win = false;   // CBP-SP with the paper-literal stop (CBP_STOP_WINDOW)
+  bool self_last = false;  // CBP-SP, one frame per group: every weight-1 edge ends its row
 };
 
 // Sizes that fix the shared-memory and workspace layout of a launch.
@@ -190,7 +191,7 @@ cudaError_t launch_decoder(const Variant& v, const KParams& p, int grid, int thr
 cudaError_t decoder_func_attrs(const Variant& v, cudaFuncAttributes* a);
 cudaError_t decoder_set_smem(const Variant& v, int bytes);
 cudaError_t decoder_occupancy(const Variant& v, int threads, size_t smem, int* ctas);
-void* sp_kernel_ptr(bool chk_shared, int fpt, bool wide);  // cbp_sp.cu
+void* sp_kernel_ptr(bool chk_shared, int fpt, bool wide, bool self_last);  // cbp_sp.cu
 void* sp_multi_kernel_ptr(bool chk_shared, int fpt);        // cbp_sp.cu
 void* sp_win_kernel_ptr(bool chk_shared);                   // cbp_sp.cu
 cudaError_t launch_multi(bool chk_shared, int fpt, const MultiParams& mp, int grid, int threads,

@@ -71,7 +71,7 @@ struct Chunk {
 
 // Loads of a chunk: (Q*, phi) of each variable, S of its predecessor check c_j, and
 // the edge's own R slot (read only once the frame is past its first sweep).
-template <int FPT, int CH, bool WIN>
+template <int FPT, int CH, bool WIN, bool NOSELF = false>
 __device__ __forceinline__ void load_chunk(Chunk<FPT, CH>& c, int kb, int k1,
                                            const SpEdge* __restrict__ s_spe, int z, int Z,
                                            bool later, const float* QP, const float* SV,
@@ -88,7 +88,7 @@ __device__ __forceinline__ void load_chunk(Chunk<FPT, CH>& c, int kb, int k1,
       c.fl[j] = se.x;
       c.qoff[j] = static_cast<int>(se.x & kSpMask) + z - (z >= tq ? Z : 0);
       c.roff[j] = static_cast<int>(se.z) + z - uj;
-      if (se.x & kSpSelf) {
+      if (!NOSELF && (se.x & kSpSelf)) {
         LV::ld_pair(SV, c.qoff[j], c.q[j], c.ph[j]);
       } else {
         LV::ld_pair(QP, c.qoff[j], c.q[j], c.ph[j]);
@@ -110,7 +110,7 @@ __device__ __forceinline__ void load_chunk(Chunk<FPT, CH>& c, int kb, int k1,
 // WIN (paper-literal stop, one frame per group): the posterior Lambda = Q* + R^new of
 // Eq. (s4e20) is compared with the variable's previous one (sign bit in pbits); a flip
 // toggles the bit and is recorded in fmask (bit = edge position in the row).
-template <int FPT, int CH, bool WIN>
+template <int FPT, int CH, bool WIN, bool NOSELF = false>
 __device__ __forceinline__ void update_chunk(const Chunk<FPT, CH>& c, int kb, int k1,
                                              const int* t, float* Sacc, uint32_t* sig,
                                              float xlo, const float4* __restrict__ tab,
@@ -120,7 +120,7 @@ __device__ __forceinline__ void update_chunk(const Chunk<FPT, CH>& c, int kb, in
 #pragma unroll
   for (int j = 0; j < CH; ++j) {
     if (kb + j < k1) {
-      const bool self = c.fl[j] & kSpSelf;
+      const bool self = !NOSELF && (c.fl[j] & kSpSelf);
       const bool first_row = c.fl[j] & kSpFirst;
       float Rn[FPT], qn[FPT], phn[FPT];
       bool store_r = false;
@@ -167,7 +167,10 @@ __device__ __forceinline__ void update_chunk(const Chunk<FPT, CH>& c, int kb, in
 // current chunk's updates when DB (they never alias: a row reads its own R slots, the
 // beliefs of other rows and distinct variables, and writes predecessor R slots, its
 // variables and its own beliefs).
-template <int FPT, int CH, bool DB, bool WIN>
+// SELFLAST: the code's weight-1 edges are each the last edge of their row (one per row at
+// most, checked on the host), so the chunk loop runs without the weight-1 branches and
+// that edge follows on its own -- still last in the column order of the fold.
+template <int FPT, int CH, bool DB, bool WIN, bool SELFLAST>
 __device__ __forceinline__ void row_edges(int k0, int k1, const SpEdge* __restrict__ s_spe,
                                           int z, int Z, bool later, const int* t, float* Sacc,
                                           uint32_t* sig, float xlo,
@@ -191,6 +194,21 @@ __device__ __forceinline__ void row_edges(int k0, int k1, const SpEdge* __restri
                                  fmask);
       kb += CH;
       if (kb >= k1) break;
+    }
+  } else if (SELFLAST) {
+    const bool has_self = (s_spe[k1 - 1].x & kSpSelf) != 0;
+    const int km = has_self ? k1 - 1 : k1;
+    for (int kb = k0; kb < km; kb += CH) {
+      Chunk<FPT, CH> A;
+      load_chunk<FPT, CH, WIN, true>(A, kb, km, s_spe, z, Z, later, QP, SV, S, R, g_edges);
+      update_chunk<FPT, CH, WIN, true>(A, kb, km, t, Sacc, sig, xlo, tab, QP, SV, R, pbits, k0,
+                                       fmask);
+    }
+    if (has_self) {
+      Chunk<FPT, 1> A;
+      load_chunk<FPT, 1, WIN>(A, k1 - 1, k1, s_spe, z, Z, later, QP, SV, S, R, g_edges);
+      update_chunk<FPT, 1, WIN>(A, k1 - 1, k1, t, Sacc, sig, xlo, tab, QP, SV, R, pbits, k0,
+                                fmask);
     }
   } else {
     for (int kb = k0; kb < k1; kb += CH) {
@@ -242,7 +260,7 @@ __device__ __forceinline__ void window_scan(const unsigned char* ok, int Z, int 
 // every thread of the team); a group whose window fills stops in the middle of the row
 // at that check: lanes after it undo their posterior-sign updates, and `halted` keeps
 // the group idle for the rest of the sweep.
-template <int FPT, int CH, bool DB, bool WIN>
+template <int FPT, int CH, bool DB, bool WIN, bool SELFLAST>
 __device__ __forceinline__ void sweep_rows(int mb, bool any, const int* s_rptr,
                                            const SpEdge* __restrict__ s_spe, int z, int Z,
                                            bool later, const int* t, float xlo,
@@ -274,8 +292,8 @@ __device__ __forceinline__ void sweep_rows(int mb, bool any, const int* s_rptr,
         Sacc[h] = 0.0f;
         sig[h] = 0;
       }
-      row_edges<FPT, CH, DB, WIN>(k0, k1, s_spe, z, Z, later, t, Sacc, sig, xlo, tab, QP, SV,
-                                  S, R, g_edges, pbits, fmask);
+      row_edges<FPT, CH, DB, WIN, SELFLAST>(k0, k1, s_spe, z, Z, later, t, Sacc, sig, xlo, tab,
+                                            QP, SV, S, R, g_edges, pbits, fmask);
       float sv[FPT];
 #pragma unroll
       for (int h = 0; h < FPT; ++h)  // Sacc >= 0: its sign bit is free for sgn(Omega)
@@ -306,7 +324,7 @@ __device__ __forceinline__ void sweep_rows(int mb, bool any, const int* s_rptr,
 // Decode frames frame0, frame0 + 1, ... of one code with the lane groups of this CTA:
 // frame slot k starts at frame0 + k and advances by `stride` when its frame stops, until
 // it passes `end`.  Returns when every slot of the CTA is idle.
-template <bool CHKS, int FPT, int CH, bool DB, bool WIN = false>
+template <bool CHKS, int FPT, int CH, bool DB, bool WIN = false, bool SELFLAST = false>
 __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride, int end,
                                         unsigned char* smem, bool load_tab) {
   static_assert(!WIN || FPT == 1, "the paper-literal stop runs one frame per lane group");
@@ -416,8 +434,9 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
 #pragma unroll
     for (int h = 0; h < FPT; ++h) later |= t[h] > 1;
     bool halted = false;
-    sweep_rows<FPT, CH, DB, WIN>(p.mb, any, s_rptr, s_spe, z, Z, later, t, xlo, tab, QP, SV, S,
-                                 R, bar_id, bar_n, p.edges, bits, wst, okb, M, halted);
+    sweep_rows<FPT, CH, DB, WIN, SELFLAST>(p.mb, any, s_rptr, s_spe, z, Z, later, t, xlo, tab,
+                                           QP, SV, S, R, bar_id, bar_n, p.edges, bits, wst,
+                                           okb, M, halted);
     bool done[FPT];
     if constexpr (WIN) {
       // Step 3: the hard decisions of the latest V2C phase; iters = the sweep in which
@@ -554,10 +573,11 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
   }
 }
 
-template <bool CHKS, int FPT, int CH, bool DB, int MAXT>
+template <bool CHKS, int FPT, int CH, bool DB, int MAXT, bool SELFLAST = false>
 __global__ void __launch_bounds__(MAXT, 1) cbp_sp_kernel(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  sp_body<CHKS, FPT, CH, DB>(p, blockIdx.x * p.F * FPT, p.slots, p.batch, smem, true);
+  sp_body<CHKS, FPT, CH, DB, false, SELFLAST>(p, blockIdx.x * p.F * FPT, p.slots, p.batch,
+                                               smem, true);
 }
 
 // The paper-literal stop of Eq. (s4e24) with the Step 3 output (one frame per group).
@@ -610,7 +630,7 @@ void* sp_win_kernel_ptr(bool chk_shared) {
                     : reinterpret_cast<void*>(&cbp_sp_win_kernel<false>);
 }
 
-void* sp_kernel_ptr(bool chk_shared, int fpt, bool wide) {
+void* sp_kernel_ptr(bool chk_shared, int fpt, bool wide, bool self_last) {
   // wide: up to 1024 threads per CTA (Z > 512), fewer registers per thread
   if (wide)
     return chk_shared ? reinterpret_cast<void*>(&cbp_sp_kernel<true, 1, 2, true, 1024>)
@@ -620,6 +640,9 @@ void* sp_kernel_ptr(bool chk_shared, int fpt, bool wide) {
                       : reinterpret_cast<void*>(&cbp_sp_kernel<false, 2, 4, true, 384>);
   // one frame per lane group, up to 768 threads: two 384-lane teams per CTA progress
   // independently and hide each other's memory latency
+  if (self_last)
+    return chk_shared ? reinterpret_cast<void*>(&cbp_sp_kernel<true, 1, 4, false, 768, true>)
+                      : reinterpret_cast<void*>(&cbp_sp_kernel<false, 1, 4, false, 768, true>);
   return chk_shared ? reinterpret_cast<void*>(&cbp_sp_kernel<true, 1, 4, false, 768>)
                     : reinterpret_cast<void*>(&cbp_sp_kernel<false, 1, 4, false, 768>);
 }
