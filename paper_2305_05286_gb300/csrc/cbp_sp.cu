@@ -198,7 +198,15 @@ __device__ __forceinline__ void row_edges(int k0, int k1, const SpEdge* __restri
   } else if (SELFLAST) {
     const bool has_self = (s_spe[k1 - 1].x & kSpSelf) != 0;
     const int km = has_self ? k1 - 1 : k1;
-    for (int kb = k0; kb < km; kb += CH) {
+    int kb = k0;
+    for (; kb + CH <= km; kb += CH) {  // whole chunks: the edge guards fold away
+      Chunk<FPT, CH> A;
+      load_chunk<FPT, CH, WIN, true>(A, kb, kb + CH, s_spe, z, Z, later, QP, SV, S, R,
+                                     g_edges);
+      update_chunk<FPT, CH, WIN, true>(A, kb, kb + CH, t, Sacc, sig, xlo, tab, QP, SV, R,
+                                       pbits, k0, fmask);
+    }
+    if (kb < km) {  // the remainder, guarded
       Chunk<FPT, CH> A;
       load_chunk<FPT, CH, WIN, true>(A, kb, km, s_spe, z, Z, later, QP, SV, S, R, g_edges);
       update_chunk<FPT, CH, WIN, true>(A, kb, km, t, Sacc, sig, xlo, tab, QP, SV, R, pbits, k0,
@@ -640,9 +648,9 @@ void* sp_kernel_ptr(bool chk_shared, int fpt, bool wide, bool self_last) {
                       : reinterpret_cast<void*>(&cbp_sp_kernel<false, 2, 4, true, 384>);
   // one frame per lane group, up to 768 threads: two 384-lane teams per CTA progress
   // independently and hide each other's memory latency
-  if (self_last)
-    return chk_shared ? reinterpret_cast<void*>(&cbp_sp_kernel<true, 1, 4, false, 768, true>)
-                      : reinterpret_cast<void*>(&cbp_sp_kernel<false, 1, 4, false, 768, true>);
+  if (self_last)  // chunks of 3 measured best once whole chunks run unguarded
+    return chk_shared ? reinterpret_cast<void*>(&cbp_sp_kernel<true, 1, 3, false, 768, true>)
+                      : reinterpret_cast<void*>(&cbp_sp_kernel<false, 1, 3, false, 768, true>);
   return chk_shared ? reinterpret_cast<void*>(&cbp_sp_kernel<true, 1, 4, false, 768>)
                     : reinterpret_cast<void*>(&cbp_sp_kernel<false, 1, 4, false, 768>);
 }
