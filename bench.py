@@ -46,9 +46,9 @@ OPS_EDGE = {"cbp_sp": 64, "cbp_nms": 31, "lbp_nms": 28, "fbp_sp": 64}
 OPS_VAR = {"cbp_sp": 30, "cbp_nms": 10, "lbp_nms": 3, "fbp_sp": 5}
 OPS_SYN = 4
 # DRAM bytes (read + write) per frame-sweep of the CBP-SP kernel on the 26112-bit code, from
-# one ncu capture of 2432 frames (14.08 GB over 9699 frame-sweeps); the workspace traffic
+# one ncu capture of 2432 frames (14.11 GB over 9699 frame-sweeps); the workspace traffic
 # grows with frame-sweeps, so a launch's traffic is this times its frame-sweeps.
-TRAFFIC_PER_FRAME_SWEEP = {"cbp_sp": 14.08e9 / (2432 * 3.98808)}
+TRAFFIC_PER_FRAME_SWEEP = {"cbp_sp": 14.11e9 / (2432 * 3.98808)}
 TRAFFIC_SOURCE = "profiles/cbp_sp_kernel_n26112_2432frames.md, scaled by frame-sweeps"
 
 
