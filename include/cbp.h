@@ -274,7 +274,8 @@ int cbp_multi_workspace_bytes(const cbp_multi_item_t* items, int n_items,
 /* The launch cbp_decode_multi would use: info[0] CTAs, info[1] threads per CTA,
  * info[2] dynamic shared bytes per CTA, info[3] CTAs resident per SM, info[4] chunks,
  * info[5] 1 if check beliefs are in shared memory, info[6] frames per lane group,
- * info[7] unused (0).  `info` is a host array of 8 ints. */
+ * info[7] 1 if every code ends its rows with its weight-1 edge (the kernel instance without
+ * weight-1 branches in its edge loop runs), else 0.  `info` is a host array of 8 ints. */
 int cbp_multi_launch_info(const cbp_multi_item_t* items, int n_items,
                           const cbp_multi_opts_t* opts, int* info);
 

@@ -412,7 +412,7 @@ def multi_launch_info(codes, batches, **opts) -> dict:
     _check("cbp_multi_launch_info",
            lib().cbp_multi_launch_info(_multi_items(codes, batches), len(codes), C.byref(o), info))
     keys = ("ctas", "threads_per_cta", "shared_bytes", "ctas_per_sm", "chunks",
-            "check_state_shared", "frames_per_lane_group")
+            "check_state_shared", "frames_per_lane_group", "weight1_last")
     return dict(zip(keys, list(info)))
 
 

@@ -34,11 +34,11 @@ cudaError_t launch_decoder(const Variant& v, const KParams& p, int grid, int thr
   return cudaLaunchKernel(select_kernel(v), dim3(grid), dim3(threads), args, smem, st);
 }
 
-cudaError_t launch_multi(bool chk_shared, int fpt, const MultiParams& mp, int grid, int threads,
-                         size_t smem, cudaStream_t st) {
+cudaError_t launch_multi(bool chk_shared, int fpt, bool self_last, const MultiParams& mp, int grid,
+                         int threads, size_t smem, cudaStream_t st) {
   void* args[] = {const_cast<MultiParams*>(&mp)};
-  return cudaLaunchKernel(sp_multi_kernel_ptr(chk_shared, fpt), dim3(grid), dim3(threads), args,
-                          smem, st);
+  return cudaLaunchKernel(sp_multi_kernel_ptr(chk_shared, fpt, self_last), dim3(grid),
+                          dim3(threads), args, smem, st);
 }
 
 }  // namespace cbp

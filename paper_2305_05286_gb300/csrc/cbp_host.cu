@@ -117,8 +117,8 @@ int device_init(int dev, DeviceInfo** out) {
       if (decoder_set_smem(v, d.smem_optin) != cudaSuccess) return CBP_ECUDA;
     if (grad_set_smem(d.smem_optin) != cudaSuccess) return CBP_ECUDA;
     for (int chk = 0; chk < 2; ++chk)
-      for (int fpt = 1; fpt <= 2; ++fpt) {
-        void* k = sp_multi_kernel_ptr(chk != 0, fpt);
+      for (int fpt = 1; fpt <= 3; ++fpt) {  // 3: one frame per group, weight-1-last instance
+        void* k = sp_multi_kernel_ptr(chk != 0, fpt == 3 ? 1 : fpt, fpt == 3);
         cudaFuncAttributes fa;
         if (cudaFuncGetAttributes(&fa, k) != cudaSuccess ||
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1014,7 +1014,7 @@ namespace {
 struct MultiPlan {
   MultiParams mp{};
   int grid = 0, threads = 0, ctas_per_sm = 0, chunks = 0, fpt = 1;
-  bool chk = false;
+  bool chk = false, self_last = false;
   size_t smem = 0, ws_bytes = 0;
 };
 
@@ -1028,7 +1028,11 @@ int multi_plan_try(const cbp_multi_item_t* items, int n, int max_iter, int stop,
   DeviceInfo* di = nullptr;
   int dev = 0;
   if (int rc = current_device(&di, &dev)) return rc;
-  void* kern = sp_multi_kernel_ptr(chk, fpt);
+  // the weight-1-last instance serves a launch whose codes all qualify
+  bool self_last = fpt == 1;
+  for (int i = 0; i < n; ++i)
+    if (items[i].batch > 0 && !items[i].code->self_last) self_last = false;
+  void* kern = sp_multi_kernel_ptr(chk, fpt, self_last);
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return CBP_ECUDA;
   if (threads > fa.maxThreadsPerBlock) return CBP_EINVAL;
@@ -1039,6 +1043,7 @@ int multi_plan_try(const cbp_multi_item_t* items, int n, int max_iter, int stop,
   pl.threads = threads;
   pl.fpt = fpt;
   pl.chk = chk;
+  pl.self_last = self_last;
   const Variant v{ALG_CBP_SP, chk, fpt};
   std::vector<int> order;
   std::vector<KParams> kp(n);
@@ -1153,7 +1158,7 @@ int cbp_multi_launch_info(const cbp_multi_item_t* items, int n_items,
   info[4] = pl.chunks;
   info[5] = pl.chk ? 1 : 0;
   info[6] = pl.fpt;
-  info[7] = 0;
+  info[7] = pl.self_last ? 1 : 0;
   return CBP_OK;
 }
 
@@ -1178,7 +1183,8 @@ int cbp_decode_multi(const cbp_multi_item_t* items, int n_items, int max_iter, v
     pl.mp.code[j].ws = reinterpret_cast<float*>(ws + kCounterBytes);
   const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(pl.mp.counter, 0, sizeof(int), st) != cudaSuccess) return CBP_ECUDA;
-  return launch_multi(pl.chk, pl.fpt, pl.mp, pl.grid, pl.threads, pl.smem, st) == cudaSuccess
+  return launch_multi(pl.chk, pl.fpt, pl.self_last, pl.mp, pl.grid, pl.threads, pl.smem, st) ==
+                 cudaSuccess
              ? CBP_OK
              : CBP_ECUDA;
 }

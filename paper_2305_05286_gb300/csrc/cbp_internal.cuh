@@ -192,10 +192,10 @@ cudaError_t decoder_func_attrs(const Variant& v, cudaFuncAttributes* a);
 cudaError_t decoder_set_smem(const Variant& v, int bytes);
 cudaError_t decoder_occupancy(const Variant& v, int threads, size_t smem, int* ctas);
 void* sp_kernel_ptr(bool chk_shared, int fpt, bool wide, bool self_last);  // cbp_sp.cu
-void* sp_multi_kernel_ptr(bool chk_shared, int fpt);        // cbp_sp.cu
+void* sp_multi_kernel_ptr(bool chk_shared, int fpt, bool self_last);  // cbp_sp.cu
 void* sp_win_kernel_ptr(bool chk_shared);                   // cbp_sp.cu
-cudaError_t launch_multi(bool chk_shared, int fpt, const MultiParams& mp, int grid, int threads,
-                         size_t smem, cudaStream_t st);
+cudaError_t launch_multi(bool chk_shared, int fpt, bool self_last, const MultiParams& mp, int grid,
+                         int threads, size_t smem, cudaStream_t st);
 void* minsum_kernel_ptr(int alg, bool chk_shared);          // cbp_minsum.cu
 void* flood_kernel_ptr();              // cbp_flood.cu
 cudaError_t launch_phi(const float* x, float* y, long long n, const float4* tab, float xlo,

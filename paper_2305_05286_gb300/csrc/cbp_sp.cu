@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(768, 1) cbp_sp_win_kernel(const KParams p) {
 
 // Several codes in one persistent launch: each CTA takes chunks (code, frame range) from
 // a work counter and decodes them with that code's lane-group layout.
-template <bool CHKS, int FPT, int CH, bool DB, int MAXT>
+template <bool CHKS, int FPT, int CH, bool DB, int MAXT, bool SELFLAST = false>
 __global__ void __launch_bounds__(MAXT, 1) cbp_sp_multi_kernel(const MultiParams mp) {
   extern __shared__ __align__(16) unsigned char smem[];
   // the chunk's code parameters live in shared memory (read like kernel parameters)
@@ -618,17 +618,22 @@ __global__ void __launch_bounds__(MAXT, 1) cbp_sp_multi_kernel(const MultiParams
     }
     __syncthreads();
     if (s_chunk[0] >= total) break;
-    sp_body<CHKS, FPT, CH, DB>(s_p, s_chunk[1], s_p.F * FPT, s_p.batch, smem, first_chunk);
+    sp_body<CHKS, FPT, CH, DB, false, SELFLAST>(s_p, s_chunk[1], s_p.F * FPT, s_p.batch, smem,
+                                               first_chunk);
     __syncthreads();
   }
 }
 
 }  // namespace
 
-void* sp_multi_kernel_ptr(bool chk_shared, int fpt) {
+void* sp_multi_kernel_ptr(bool chk_shared, int fpt, bool self_last) {
   if (fpt == 2)
     return chk_shared ? reinterpret_cast<void*>(&cbp_sp_multi_kernel<true, 2, 4, true, 384>)
                       : reinterpret_cast<void*>(&cbp_sp_multi_kernel<false, 2, 4, true, 384>);
+  if (self_last)  // every item's code ends its rows with the weight-1 edge
+    return chk_shared
+               ? reinterpret_cast<void*>(&cbp_sp_multi_kernel<true, 1, 3, false, 768, true>)
+               : reinterpret_cast<void*>(&cbp_sp_multi_kernel<false, 1, 3, false, 768, true>);
   return chk_shared ? reinterpret_cast<void*>(&cbp_sp_multi_kernel<true, 1, 4, false, 768>)
                     : reinterpret_cast<void*>(&cbp_sp_multi_kernel<false, 1, 4, false, 768>);
 }

@@ -201,3 +201,30 @@ def test_tuner_cache(mixed, tmp_path):
     # batch sizes in the same power-of-two bucket share the entry
     assert tune.cache_key(codes, [60] * 8) == tune.cache_key(codes, [64] * 8)
     assert tune.cache_key(codes, [65] * 8) != tune.cache_key(codes, [64] * 8)
+
+
+def test_multi_weight1_last_instance_choice(mixed):
+    # All eight mixed codes end the rows that hold their weight-1 column with it, so the
+    # launch runs the instance without weight-1 branches; one code whose weight-1 column
+    # comes first in its row switches the whole launch to the generic instance.
+    qcs, codes = mixed
+    batches = [40] * 8
+    assert cbp.multi_launch_info(codes, batches)["weight1_last"] == 1
+    assert cbp.multi_launch_info(codes, batches, frames_per_group=2)["weight1_last"] == 0
+    base = qcs[2].base
+    w1 = int(np.nonzero((base >= 0).sum(0) == 1)[0][0])
+    perm = [w1] + [c for c in range(base.shape[1]) if c != w1]
+    q_first = I.QCCode(np.ascontiguousarray(base[:, perm]), qcs[2].Z)
+    c_first = cbp.Code.from_qc(q_first)
+    codes2, qcs2 = codes[:7] + [c_first], qcs[:7] + [q_first]
+    assert cbp.multi_launch_info(codes2, batches)["weight1_last"] == 0
+    # a code with no frames does not decide the instance
+    assert cbp.multi_launch_info(codes2, batches[:7] + [0])["weight1_last"] == 1
+    llrs = frames_for(qcs2, [90, 80, 70, 60, 50, 40, 30, 120], seed=9500)
+    got = run_multi(codes2, llrs, max_iter=15)
+    for c, a, (hard, iters) in zip(codes2, llrs, got):
+        h1, i1 = run_single(c, a, max_iter=15)
+        assert np.array_equal(iters, i1) and np.array_equal(hard, h1), f"Z={c.Z}"
+    ref = O.OracleCode(q_first.base, q_first.Z).decode(llrs[7], alg="cbp_sp", max_iter=15,
+                                                        threads=THREADS)
+    assert np.array_equal(got[7][1], ref["iters"]) and np.array_equal(got[7][0], ref["hard"])

@@ -346,6 +346,27 @@ def test_every_cbp_sp_layout_variant(code576, monkeypatch, chk, fpt):
         assert_parity(run_gpu(code, fr.llr, alg, max_iter=25), ref, f"{alg} chk {chk} fpt {fpt}")
 
 
+@pytest.mark.parametrize("chk,fpt", [("0", "1"), ("1", "1"), ("1", "2")])
+@pytest.mark.parametrize("pos", [0, 11])
+def test_weight1_column_not_last_in_its_row(monkeypatch, pos, chk, fpt):
+    # Every code above ends the rows holding a weight-1 column with that column, and the
+    # planner then runs the kernel instance without weight-1 branches in its edge loop.
+    # Moving the weight-1 column to the front (or the middle) of the base matrix makes
+    # the generic instance run; the oracle decodes the permuted code on its own terms.
+    base = I.code_576().base
+    w1 = int(np.nonzero((base >= 0).sum(0) == 1)[0][0])
+    perm = [c for c in range(base.shape[1]) if c != w1]
+    perm.insert(pos, w1)
+    qc = I.QCCode(np.ascontiguousarray(base[:, perm]), 24)
+    monkeypatch.setenv("CBP_PLAN_CHK", chk)
+    monkeypatch.setenv("CBP_PLAN_FPT", fpt)
+    code = cbp.Code.from_qc(qc)
+    fr = I.make_frames(qc, 300, 2.0, seed=4300 + pos)
+    ref = O.OracleCode(qc.base, qc.Z).decode(fr.llr, alg="cbp_sp", max_iter=25, threads=THREADS)
+    assert (ref["iters"] < 0).any() and (ref["iters"] > 1).any()
+    assert_parity(run_gpu(code, fr.llr, "cbp_sp", max_iter=25), ref, f"weight-1 column at {pos}")
+
+
 @pytest.mark.parametrize("Z", [512, 1000])
 def test_lifts_above_384(Z):
     # Z = 512: one lane group in a 768-thread CTA (idle lanes, one CTA-wide team);
