@@ -159,7 +159,10 @@ int cbp_decode_host(const cbp_code_t* code, const float* llr_host, uint32_t* har
  *   info[2] CTAs per SM                 info[3] lane groups per CTA
  *   info[4] frames per lane group       info[5] 1 if the check state is in shared memory
  *   info[6] CTAs launched               info[7] lane groups per synchronising team
- * `info` is a host array of 8 ints.  Nothing is launched. */
+ *   info[8] dynamic shared bytes per CTA
+ *   info[9] 1 if the CBP-SP instance for codes whose weight-1 edges end their rows runs
+ *   info[10], info[11] reserved (0)
+ * `info` is a host array of 12 ints.  Nothing is launched. */
 int cbp_launch_info(const cbp_code_t* code, int batch, const cbp_opts_t* opts, int* info);
 
 /* ---- Weighted CBP: the differentiable decoder --------------------------------------

@@ -183,11 +183,12 @@ class Code:
 
     def launch_info(self, batch: int, alg: str = "cbp_sp", stop: str = "syndrome") -> dict:
         """The launch plan cbp_decode_ex would use (cbp_launch_info)."""
-        info = (C.c_int * 8)()
+        info = (C.c_int * 12)()
         o = _opts(alg, 0.75, stop, None)
         _check("cbp_launch_info", lib().cbp_launch_info(self._h, int(batch), C.byref(o), info))
         keys = ("frames_per_sm", "threads_per_cta", "ctas_per_sm", "lane_groups_per_cta",
-                "frames_per_lane_group", "check_state_shared", "ctas", "team_lane_groups")
+                "frames_per_lane_group", "check_state_shared", "ctas", "team_lane_groups",
+                "shared_bytes", "weight1_last")
         return dict(zip(keys, list(info)))
 
     # ------------------------------------------------------------------ decode

@@ -654,6 +654,10 @@ int cbp_launch_info(const cbp_code_t* c, int batch, const cbp_opts_t* opts, int*
   info[5] = pl.v.chk_shared ? 1 : 0;
   info[6] = pl.grid;
   info[7] = pl.team_groups;
+  info[8] = static_cast<int>(pl.smem);
+  info[9] = pl.v.self_last ? 1 : 0;
+  info[10] = 0;
+  info[11] = 0;
   return CBP_OK;
 }
 

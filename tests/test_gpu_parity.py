@@ -130,6 +130,9 @@ def test_full_size_26112_sampled(large):
     """65536 frames in the benchmark's launch configuration; 12 frames re-decoded by the oracle."""
     qc, code, oc = large
     B = 65536
+    info = code.launch_info(B)  # two 384-lane frames per SM, weight-1-last instance
+    assert info["weight1_last"] == 1 and info["frames_per_sm"] == 2
+    assert 0 < info["shared_bytes"] <= 227 * 1024
     llr, cw = I.make_frames_torch(qc, B, 1.0, seed=2100)
     hard, iters, soft = code.decode(llr, max_iter=20, alg="cbp_sp", soft=True)
     torch.cuda.synchronize()
@@ -361,6 +364,8 @@ def test_weight1_column_not_last_in_its_row(monkeypatch, pos, chk, fpt):
     monkeypatch.setenv("CBP_PLAN_CHK", chk)
     monkeypatch.setenv("CBP_PLAN_FPT", fpt)
     code = cbp.Code.from_qc(qc)
+    info = code.launch_info(300)
+    assert info["weight1_last"] == 0 and info["check_state_shared"] == int(chk)
     fr = I.make_frames(qc, 300, 2.0, seed=4300 + pos)
     ref = O.OracleCode(qc.base, qc.Z).decode(fr.llr, alg="cbp_sp", max_iter=25, threads=THREADS)
     assert (ref["iters"] < 0).any() and (ref["iters"] > 1).any()
