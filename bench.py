@@ -688,7 +688,7 @@ def main():
     ap.add_argument("--sweep-hi", type=float, default=2.0)
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-chunk", type=int, default=8192)
+    ap.add_argument("--e2e-chunk", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-frames", type=int, default=4096)

@@ -135,9 +135,12 @@ int cbp_decode_ex(const cbp_code_t* code, const float* llr, uint32_t* hard_out,
 
 /* ---- Decoding from host memory, copies overlapped with decoding -------------------
  * The same decode as cbp_decode_ex, with the LLRs and the results in host memory.  The
- * batch is cut into chunks of `chunk` frames; while chunk i is decoded on `stream`,
- * chunk i + 1 is copied in (and chunk i - 1's results out) on a second stream that the
- * call creates and releases.  Two chunk buffers live in the caller's device memory
+ * batch is cut into chunks of `chunk` frames; while chunk i is decoded, chunk i + 1 is
+ * copied in (and chunk i - 1's results out) on a copy stream.  Even chunks decode on
+ * `stream`, odd ones on a second decode stream, each with its own workspace, so the next
+ * chunk's CTAs start on the SMs that the current chunk's last frames leave idle.  The call
+ * creates and releases both extra streams, ordered after the work already queued on
+ * `stream`.  Two chunk buffers and two workspaces live in the caller's device memory
  * `dev_buf` of at least cbp_host_buffer_bytes(code, chunk, opts) bytes (256-byte
  * aligned); the library allocates no device memory.  The paper has no counterpart.
  *   llr_host    host [batch][N] fp32; hard_host [batch][ceil(N/32)] uint32;

@@ -240,7 +240,7 @@ class Code:
         return hard, iters, sb
 
     def decode_host(self, llr: torch.Tensor, max_iter: int = 30, alg: str = "cbp_sp",
-                     alpha: float = 0.75, stop: str = "syndrome", chunk: int = 16384,
+                     alpha: float = 0.75, stop: str = "syndrome", chunk: int = 4096,
                      hard: torch.Tensor | None = None, iters: torch.Tensor | None = None,
                      stream=None, sync: bool = True):
         """Decode host LLRs [B, N] float32 with the copies overlapped with decoding

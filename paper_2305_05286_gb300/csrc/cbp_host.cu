@@ -706,7 +706,7 @@ int cbp_decode(const cbp_code_t* c, const float* llr, uint32_t* hard_out, int32_
 namespace {
 
 struct HostLayout {
-  size_t llr[2], hard[2], iters[2], ws, total;
+  size_t llr[2], hard[2], iters[2], ws[2], total;
 };
 
 size_t round256(size_t n) { return (n + 255) & ~static_cast<size_t>(255); }
@@ -727,8 +727,11 @@ HostLayout host_layout(const cbp_code* c, int chunk, size_t ws_bytes) {
     L.iters[b] = off;
     off += round256(static_cast<size_t>(chunk) * sizeof(int32_t));
   }
-  L.ws = off;
-  L.total = off + ws_bytes;
+  for (int b = 0; b < 2; ++b) {  // chunks i and i + 1 may decode at the same time
+    L.ws[b] = off;
+    off += round256(ws_bytes);
+  }
+  L.total = off;
   return L;
 }
 
@@ -779,7 +782,9 @@ int cbp_decode_host(const cbp_code_t* c, const float* llr_host, uint32_t* hard_h
   const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t words = (static_cast<size_t>(c->N) + 31) / 32;
   const int n_chunks = static_cast<int>((static_cast<long long>(batch) + chunk - 1) / chunk);
-  cudaStream_t cs = nullptr;
+  // chunks decode alternately on `stream` and on ks, each with its own workspace, so
+  // that the CTAs of chunk i + 1 take the SMs that chunk i's tail leaves idle; cs copies
+  cudaStream_t cs = nullptr, ks = nullptr;
   cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_dec[2] = {nullptr, nullptr}, ev_done = nullptr;
   int rc = CBP_OK;
   auto ok = [&](cudaError_t e) {
@@ -795,13 +800,15 @@ int cbp_decode_host(const cbp_code_t* c, const float* llr_host, uint32_t* hard_h
            ok(cudaEventRecord(ev_in[b], cs));
   };
   if (ok(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) &&
+      ok(cudaStreamCreateWithFlags(&ks, cudaStreamNonBlocking)) &&
       ok(cudaEventCreateWithFlags(&ev_in[0], cudaEventDisableTiming)) &&
       ok(cudaEventCreateWithFlags(&ev_in[1], cudaEventDisableTiming)) &&
       ok(cudaEventCreateWithFlags(&ev_dec[0], cudaEventDisableTiming)) &&
       ok(cudaEventCreateWithFlags(&ev_dec[1], cudaEventDisableTiming)) &&
       ok(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming))) {
-    // the copy stream starts after the work the caller queued on `stream` before this call
-    ok(cudaEventRecord(ev_done, st)) && ok(cudaStreamWaitEvent(cs, ev_done, 0));
+    // the copy and decode streams start after the work the caller queued on `stream`
+    ok(cudaEventRecord(ev_done, st)) && ok(cudaStreamWaitEvent(cs, ev_done, 0)) &&
+        ok(cudaStreamWaitEvent(ks, ev_done, 0));
     for (int i = 0; i < std::min(2, n_chunks) && rc == CBP_OK; ++i) h2d(i);
     for (int i = 0; i < n_chunks && rc == CBP_OK; ++i) {
       const int b = i & 1, n = frames(i);
@@ -809,10 +816,11 @@ int cbp_decode_host(const cbp_code_t* c, const float* llr_host, uint32_t* hard_h
       p.llr = reinterpret_cast<const float*>(base + L.llr[b]);
       p.hard = reinterpret_cast<uint32_t*>(base + L.hard[b]);
       p.iters = reinterpret_cast<int32_t*>(base + L.iters[b]);
-      p.ws = reinterpret_cast<float*>(base + L.ws);
-      if (!ok(cudaStreamWaitEvent(st, ev_in[b], 0)) ||
-          !ok(launch_decoder(pl.v, p, pl.grid, pl.threads, pl.smem, st)) ||
-          !ok(cudaEventRecord(ev_dec[b], st)) || !ok(cudaStreamWaitEvent(cs, ev_dec[b], 0)) ||
+      p.ws = reinterpret_cast<float*>(base + L.ws[b]);
+      const cudaStream_t kst = b ? ks : st;
+      if (!ok(cudaStreamWaitEvent(kst, ev_in[b], 0)) ||
+          !ok(launch_decoder(pl.v, p, pl.grid, pl.threads, pl.smem, kst)) ||
+          !ok(cudaEventRecord(ev_dec[b], kst)) || !ok(cudaStreamWaitEvent(cs, ev_dec[b], 0)) ||
           !ok(cudaMemcpyAsync(hard_host + static_cast<size_t>(i) * chunk * words,
                               base + L.hard[b], static_cast<size_t>(n) * words * sizeof(uint32_t),
                               cudaMemcpyDeviceToHost, cs)) ||
@@ -823,13 +831,14 @@ int cbp_decode_host(const cbp_code_t* c, const float* llr_host, uint32_t* hard_h
       // buffer b is free again once chunk i is decoded and its results copied out
       if (i + 2 < n_chunks) h2d(i + 2);
     }
-    // `stream` completes after the last copy
+    // `stream` completes after the last copy (which follows every decode)
     if (rc == CBP_OK) ok(cudaEventRecord(ev_done, cs)) && ok(cudaStreamWaitEvent(st, ev_done, 0));
   }
   // released once the queued work has finished
   for (cudaEvent_t e : {ev_in[0], ev_in[1], ev_dec[0], ev_dec[1], ev_done})
     if (e) cudaEventDestroy(e);
   if (cs) cudaStreamDestroy(cs);
+  if (ks) cudaStreamDestroy(ks);
   return rc;
 }
 
