@@ -512,7 +512,10 @@ def run_multi_bench(args):
     its = [torch.empty((b,), dtype=torch.int32, device=dev) for b in batches]
 
     t0 = time.perf_counter()
-    best, table = tune.tune_multi(codes, llrs, MAX_ITER, reps=2)
+    if args.no_tune:  # the library's default launch options (a fixed shape for profiling)
+        best, table = {}, []
+    else:
+        best, table = tune.tune_multi(codes, llrs, MAX_ITER, reps=2)
     tune_s = time.perf_counter() - t0
     ws = torch.empty(max(cbp.multi_workspace_bytes(codes, batches, **best), 256),
                      dtype=torch.uint8, device=dev)
@@ -675,6 +678,8 @@ def main():
                     help="min-sum normalisation for --sweep (the bench line uses 0.75)")
     ap.add_argument("--learned", action="store_true")
     ap.add_argument("--multi", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="--multi: skip the autotuner and use the library's default options")
     ap.add_argument("--nms-study", action="store_true")
     ap.add_argument("--paper-rerun", action="store_true")
     ap.add_argument("--study-frames", type=int, default=100000)

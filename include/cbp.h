@@ -249,6 +249,11 @@ int cbp_decode_noalloc(const cbp_code_t* code, const float* llr, uint32_t* hard_
  *   ctas_per_sm       CTAs resident per SM the shared-memory split aims at (0 = 1)
  *   rounds_per_chunk  frame rounds of a CTA's lane groups per chunk (0 = 4)
  *   stop_mode         cbp_stop (0 = CBP_STOP_SYNDROME)
+ *   tail_percent      the last tail_percent % of each item's frames (rounded up to whole
+ *                     rounds) are decoded in chunks of one round after all other chunks,
+ *                     so that the launch ends on short chunks; 1..100, 0 = 20, -1 = none
+ * Work order: every item's main chunks, heaviest item first, then the items' tail chunks
+ * in the same order.
  * The workspace holds a work counter (the call zeroes it with cudaMemsetAsync on
  * `stream` before the launch, so the call can be captured into a CUDA graph) and the
  * per-CTA decoder state.  Errors: CBP_EINVAL (bad pointers, alignment, options,
@@ -271,6 +276,7 @@ typedef struct cbp_multi_opts {
   int ctas_per_sm;
   int rounds_per_chunk;
   int stop_mode;
+  int tail_percent;
 } cbp_multi_opts_t;
 
 /* Bytes of workspace cbp_decode_multi needs for these items and options. */

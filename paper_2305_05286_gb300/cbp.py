@@ -52,7 +52,8 @@ class _MultiItem(C.Structure):
 
 class _MultiOpts(C.Structure):
     _fields_ = [("frames_per_group", C.c_int), ("chk_shared", C.c_int), ("threads", C.c_int),
-                ("ctas_per_sm", C.c_int), ("rounds_per_chunk", C.c_int), ("stop_mode", C.c_int)]
+                ("ctas_per_sm", C.c_int), ("rounds_per_chunk", C.c_int), ("stop_mode", C.c_int),
+                ("tail_percent", C.c_int)]
 
 
 _lock = threading.Lock()
@@ -370,10 +371,11 @@ def weighted_cbp(code: Code, llr: torch.Tensor, weights: torch.Tensor, T: int,
 # ----------------------------------------------------------------------------- several codes
 def multi_opts(frames_per_group: int = 0, chk_shared: int = -1, threads: int = 0,
                ctas_per_sm: int = 0, rounds_per_chunk: int = 0,
-               stop: str = "syndrome") -> _MultiOpts:
-    """Launch options of cbp_decode_multi (0 / -1 = the library's default)."""
+               stop: str = "syndrome", tail_percent: int = 0) -> _MultiOpts:
+    """Launch options of cbp_decode_multi (0 / -1 = the library's default; tail_percent
+    -1 = no tail of one-round chunks)."""
     return _MultiOpts(int(frames_per_group), int(chk_shared), int(threads), int(ctas_per_sm),
-                      int(rounds_per_chunk), STOPS[stop])
+                      int(rounds_per_chunk), STOPS[stop], int(tail_percent))
 
 
 def _multi_items(codes, batches, llrs=None, hards=None, iters=None):

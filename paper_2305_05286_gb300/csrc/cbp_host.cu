@@ -1032,12 +1032,16 @@ struct MultiPlan {
 };
 
 constexpr size_t kCounterBytes = 256;  // work counter at the start of the workspace
+constexpr int kDefaultTailPercent = 20;  // cbp_multi_opts_t::tail_percent == 0
 
-// Lane groups, shared memory and workspace of every item under one CTA shape; items
-// ordered heaviest chunk first (a chunk's time grows with the code's base entries and
-// with the frame rounds it holds).
+// Lane groups, shared memory and workspace of every item under one CTA shape, and the
+// work list: each item's main segment (chunks of `rounds` frame rounds), heaviest chunk
+// first (a chunk's time grows with the code's base entries and with the frame rounds it
+// holds), then the items' tail segments in the same order: the last tail_pct percent of
+// each item's frames in chunks of one round, so that the launch ends on short chunks.
 int multi_plan_try(const cbp_multi_item_t* items, int n, int max_iter, int stop, bool chk,
-                   int fpt, int threads, int ctas_target, int rounds, MultiPlan* out) {
+                   int fpt, int threads, int ctas_target, int rounds, int tail_pct,
+                   MultiPlan* out) {
   DeviceInfo* di = nullptr;
   int dev = 0;
   if (int rc = current_device(&di, &dev)) return rc;
@@ -1060,7 +1064,7 @@ int multi_plan_try(const cbp_multi_item_t* items, int n, int max_iter, int stop,
   const Variant v{ALG_CBP_SP, chk, fpt};
   std::vector<int> order;
   std::vector<KParams> kp(n);
-  std::vector<int> cf(n, 0);
+  std::vector<int> cf(n, 0), cf1(n, 0);
   long long ws_cta = 0;
   for (int i = 0; i < n; ++i) {
     const cbp_code* c = items[i].code;
@@ -1089,6 +1093,7 @@ int multi_plan_try(const cbp_multi_item_t* items, int n, int max_iter, int stop,
     kp[i].hard = items[i].hard_out;
     kp[i].iters = items[i].iters_out;
     cf[i] = G * fpt * rounds;
+    cf1[i] = G * fpt;
     pl.smem = std::max(pl.smem, smem);
     ws_cta = std::max<long long>(ws_cta, static_cast<long long>(G) * cp.ws.slot);
     order.push_back(i);
@@ -1097,16 +1102,35 @@ int multi_plan_try(const cbp_multi_item_t* items, int n, int max_iter, int stop,
     return 1LL * items[a].code->nnzb * rounds > 1LL * items[b].code->nnzb * rounds;
   });
   pl.mp.ncodes = static_cast<int>(order.size());
-  long long chunks = 0;
+  std::vector<int> split(n, 0);  // first frame of the item's tail segment
   for (size_t j = 0; j < order.size(); ++j) {
-    const int i = order[j];
+    const int i = order[j], b = items[i].batch;
     kp[i].ws_cta = ws_cta;
     pl.mp.code[j] = kp[i];
-    pl.mp.chunk_frames[j] = cf[i];
-    chunks += (items[i].batch + cf[i] - 1) / cf[i];
-    if (chunks > (1LL << 30)) return CBP_EUNSUPPORTED;
-    pl.mp.chunk_end[j] = static_cast<int>(chunks);
+    long long tail = (1LL * b * tail_pct + 99) / 100;
+    tail = std::min<long long>(b, (tail + cf1[i] - 1) / cf1[i] * cf1[i]);
+    split[i] = b - static_cast<int>(tail);
   }
+  long long chunks = 0;
+  int ns = 0;
+  auto add_seg = [&](int j, int f0, int f1, int frames) {
+    if (f1 <= f0) return true;
+    chunks += (f1 - f0 + frames - 1) / frames;
+    if (chunks > (1LL << 30)) return false;
+    pl.mp.seg_code[ns] = j;
+    pl.mp.seg_frame0[ns] = f0;
+    pl.mp.seg_frame1[ns] = f1;
+    pl.mp.seg_frames[ns] = frames;
+    pl.mp.seg_end[ns] = static_cast<int>(chunks);
+    ++ns;
+    return true;
+  };
+  for (size_t j = 0; j < order.size(); ++j)
+    if (!add_seg(static_cast<int>(j), 0, split[order[j]], cf[order[j]])) return CBP_EUNSUPPORTED;
+  for (size_t j = 0; j < order.size(); ++j)
+    if (!add_seg(static_cast<int>(j), split[order[j]], items[order[j]].batch, cf1[order[j]]))
+      return CBP_EUNSUPPORTED;
+  pl.mp.nseg = ns;
   pl.chunks = static_cast<int>(chunks);
   int ctas = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, kern, threads, pl.smem) != cudaSuccess)
@@ -1135,15 +1159,18 @@ int multi_plan(const cbp_multi_item_t* items, int n, const cbp_multi_opts_t* o, 
   const int rounds = d.rounds_per_chunk == 0 ? 4 : d.rounds_per_chunk;
   if (ctas < 1 || ctas > 32 || rounds < 1 || rounds > 4096) return CBP_EINVAL;
   if (d.stop_mode != CBP_STOP_SYNDROME && d.stop_mode != CBP_STOP_NONE) return CBP_EINVAL;
+  if (d.tail_percent < -1 || d.tail_percent > 100) return CBP_EINVAL;
+  const int tail = d.tail_percent == 0 ? kDefaultTailPercent : std::max(0, d.tail_percent);
   for (int i = 0; i < n; ++i)
     if (!items[i].code || items[i].batch < 0) return CBP_EINVAL;
   if (d.chk_shared == 0 || d.chk_shared == 1)
     return multi_plan_try(items, n, max_iter, d.stop_mode, d.chk_shared == 1, fpt, threads, ctas,
-                          rounds, out);
+                          rounds, tail, out);
   const int rc = multi_plan_try(items, n, max_iter, d.stop_mode, true, fpt, threads, ctas, rounds,
-                                out);
+                                tail, out);
   if (rc != CBP_EUNSUPPORTED) return rc;
-  return multi_plan_try(items, n, max_iter, d.stop_mode, false, fpt, threads, ctas, rounds, out);
+  return multi_plan_try(items, n, max_iter, d.stop_mode, false, fpt, threads, ctas, rounds, tail,
+                        out);
 }
 
 }  // namespace

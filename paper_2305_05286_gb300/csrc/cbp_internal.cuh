@@ -153,11 +153,19 @@ struct KParams {
 };
 
 // Several codes in one launch (CBP-SP): per-code parameters and the chunk list.
+// The work list is a sequence of segments; a segment is a frame range [frame0, frame1)
+// of one code cut into chunks of `frames` frames.  Each code has a main segment and,
+// optionally, a tail segment of one-round chunks placed after every main segment.
 constexpr int kMaxMultiCodes = 8;
+constexpr int kMaxMultiSegs = 2 * kMaxMultiCodes;
 struct MultiParams {
   KParams code[kMaxMultiCodes];
-  int chunk_end[kMaxMultiCodes];     // exclusive prefix end of each code's chunks
-  int chunk_frames[kMaxMultiCodes];  // frames per chunk of each code
+  int seg_code[kMaxMultiSegs];    // index into code[]
+  int seg_end[kMaxMultiSegs];     // exclusive prefix end of the segments' chunks
+  int seg_frame0[kMaxMultiSegs];  // first frame of the segment
+  int seg_frame1[kMaxMultiSegs];  // end of the segment's frames
+  int seg_frames[kMaxMultiSegs];  // frames per chunk
+  int nseg;
   int* counter;                      // next chunk (zeroed before the launch)
   int ncodes;
 };

@@ -596,24 +596,25 @@ __global__ void __launch_bounds__(768, 1) cbp_sp_win_kernel(const KParams p) {
 }
 
 // Several codes in one persistent launch: each CTA takes chunks (code, frame range) from
-// a work counter and decodes them with that code's lane-group layout.
+// a work counter, in the order of the segment list, and decodes them with that code's
+// lane-group layout.
 template <bool CHKS, int FPT, int CH, bool DB, int MAXT, bool SELFLAST = false>
 __global__ void __launch_bounds__(MAXT, 1) cbp_sp_multi_kernel(const MultiParams mp) {
   extern __shared__ __align__(16) unsigned char smem[];
   // the chunk's code parameters live in shared memory (read like kernel parameters)
   __shared__ KParams s_p;
   __shared__ int s_chunk[2];  // chunk index, frame range start
-  const int total = mp.chunk_end[mp.ncodes - 1];
+  const int total = mp.seg_end[mp.nseg - 1];
   for (bool first_chunk = true;; first_chunk = false) {
     if (threadIdx.x == 0) {
       const int c = atomicAdd(mp.counter, 1);
       s_chunk[0] = c;
       if (c < total) {
         int k = 0;
-        while (c >= mp.chunk_end[k]) ++k;
-        s_p = mp.code[k];
-        s_chunk[1] = (k == 0 ? c : c - mp.chunk_end[k - 1]) * mp.chunk_frames[k];
-        s_p.batch = min(s_chunk[1] + mp.chunk_frames[k], s_p.batch);  // range end
+        while (c >= mp.seg_end[k]) ++k;
+        s_p = mp.code[mp.seg_code[k]];
+        s_chunk[1] = mp.seg_frame0[k] + (k == 0 ? c : c - mp.seg_end[k - 1]) * mp.seg_frames[k];
+        s_p.batch = min(s_chunk[1] + mp.seg_frames[k], mp.seg_frame1[k]);  // range end
       }
     }
     __syncthreads();

@@ -1,9 +1,10 @@
 """Launch autotuner for the several-codes decoder (cbp_decode_multi).
 
 The library's default launch shape (one 768-thread CTA per SM, four frame rounds per
-chunk) is a safe choice, not always the fastest: small lifting sizes leave lanes
-idle, two interleaved frames per lane group hide more latency, and smaller chunks
-balance better when few frames are left.  `tune_multi` times each candidate option
+chunk, the last 20 % of each item's frames in one-round chunks) is a safe choice, not
+always the fastest: small lifting sizes leave lanes idle, two interleaved frames per
+lane group hide more latency, and the size of chunks and of the one-round tail trade
+per-chunk overhead against idle SMs at the end of the launch.  `tune_multi` times each candidate option
 set on the caller's own frames with CUDA events and returns the fastest.  All
 decoding runs in libcbp; this module only chooses among its launch options.
 """
@@ -16,18 +17,20 @@ import torch
 from . import cbp
 
 
-def candidates(codes, fpts=(1, 2), chks=(1, 0), ctas=(1, 2), rounds=(1, 2, 4, 8)):
+def candidates(codes, fpts=(1, 2), chks=(1, 0), ctas=(1, 2), rounds=(1, 2, 4, 8),
+               tails=(-1, 20, 50)):
     """Option sets worth timing: every combination whose CTA can hold each code's
-    lifting size (threads >= Z) and that the library can plan."""
+    lifting size (threads >= Z) and that the library can plan.  The tail of one-round
+    chunks only matters when chunks hold more than one round."""
     zmax = max(c.Z for c in codes)
     out = []
-    for fpt, chk, cps, r in itertools.product(fpts, chks, ctas, rounds):
+    for fpt, chk, cps, r, tail in itertools.product(fpts, chks, ctas, rounds, tails):
         tmax = 384 if fpt == 2 else 768
         threads = tmax // cps if cps > 1 and tmax // cps >= zmax else tmax
-        if threads < zmax:
+        if threads < zmax or (r == 1 and tail != tails[0]):
             continue
         out.append(dict(frames_per_group=fpt, chk_shared=chk, threads=threads,
-                        ctas_per_sm=cps, rounds_per_chunk=r))
+                        ctas_per_sm=cps, rounds_per_chunk=r, tail_percent=tail))
     return out
 
 

@@ -69,7 +69,10 @@ OPTS = [dict(),
         dict(chk_shared=0),
         dict(frames_per_group=2, chk_shared=0, rounds_per_chunk=1),
         dict(threads=384, ctas_per_sm=2, rounds_per_chunk=3),
-        dict(rounds_per_chunk=1, ctas_per_sm=2)]
+        dict(rounds_per_chunk=1, ctas_per_sm=2),
+        dict(tail_percent=-1),
+        dict(tail_percent=100, rounds_per_chunk=8),
+        dict(tail_percent=35, frames_per_group=2, rounds_per_chunk=5)]
 
 
 @pytest.mark.parametrize("opts", OPTS, ids=[str(o) for o in OPTS])
@@ -159,7 +162,8 @@ def test_multi_errors(mixed):
     assert L.cbp_decode_multi(items, 1, 10, ws.data_ptr(), ws.numel(), None, C.byref(o)) == -4
     # invalid options and sweep limit
     for bad in (cbp.multi_opts(frames_per_group=3), cbp.multi_opts(threads=100),
-                cbp.multi_opts(threads=512, frames_per_group=2), cbp.multi_opts(ctas_per_sm=-1)):
+                cbp.multi_opts(threads=512, frames_per_group=2), cbp.multi_opts(ctas_per_sm=-1),
+                cbp.multi_opts(tail_percent=101), cbp.multi_opts(tail_percent=-2)):
         assert L.cbp_decode_multi(items, 1, 10, ws.data_ptr(), ws.numel(), None, C.byref(bad)) == -1
     o = cbp.multi_opts()
     assert L.cbp_decode_multi(items, 1, 0, ws.data_ptr(), ws.numel(), None, C.byref(o)) == -1
@@ -228,3 +232,17 @@ def test_multi_weight1_last_instance_choice(mixed):
     ref = O.OracleCode(q_first.base, q_first.Z).decode(llrs[7], alg="cbp_sp", max_iter=15,
                                                         threads=THREADS)
     assert np.array_equal(got[7][1], ref["iters"]) and np.array_equal(got[7][0], ref["hard"])
+
+
+def test_multi_tail_of_one_round_chunks(mixed):
+    # the last tail_percent % of an item's frames (whole rounds) run as one-round chunks
+    qcs, codes = mixed
+    B = 1600
+    c_none = cbp.multi_launch_info([codes[7]], [B], tail_percent=-1)["chunks"]
+    G = B // (4 * c_none)  # frames per round of this code's CTA
+    assert G * 4 * c_none == B
+    assert cbp.multi_launch_info([codes[7]], [B], tail_percent=100)["chunks"] == B // G
+    tail = -(-(B * 20 // 100) // G) * G
+    want = -(-(B - tail) // (4 * G)) + tail // G
+    assert cbp.multi_launch_info([codes[7]], [B])["chunks"] == want
+    assert cbp.multi_launch_info([codes[7]], [B], tail_percent=20)["chunks"] == want
