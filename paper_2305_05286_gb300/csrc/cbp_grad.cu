@@ -61,7 +61,8 @@ struct Shared {
   BaseEdge* e;
   int* rptr;
   uint2* col;  // (last row | shift << 16)
-  float* gw;   // [T*mb]
+  float* gw;   // [T*mb] weight gradients of this CTA
+  float* w;    // [T*mb] the weights
 };
 
 __device__ Shared carve(unsigned char* smem, const GParams& p, bool load) {
@@ -76,6 +77,8 @@ __device__ Shared carve(unsigned char* smem, const GParams& p, bool load) {
   sh.col = reinterpret_cast<uint2*>(sp);
   sp += sizeof(uint2) * ((p.nb + 1) & ~1);
   sh.gw = reinterpret_cast<float*>(sp);
+  sp += sizeof(float) * p.T * p.mb;
+  sh.w = reinterpret_cast<float*>(sp);
   if (load) {
     const int tid = threadIdx.x;
     for (int i = tid; i < kPhiSegments; i += blockDim.x) sh.tab[i] = p.phi_tab[i];
@@ -85,7 +88,10 @@ __device__ Shared carve(unsigned char* smem, const GParams& p, bool load) {
       const ColEntry ce = p.cols[p.cptr[c + 1] - 1];
       sh.col[c] = make_uint2(uint32_t(ce.r) | (uint32_t(ce.s) << 16), 0u);
     }
-    for (int i = tid; i < p.T * p.mb; i += blockDim.x) sh.gw[i] = 0.0f;
+    for (int i = tid; i < p.T * p.mb; i += blockDim.x) {
+      sh.gw[i] = 0.0f;
+      sh.w[i] = p.w[i];
+    }
   }
   return sh;
 }
@@ -95,6 +101,13 @@ __device__ __forceinline__ void copy_state(float* dst, const float* src, long lo
                                            int Z) {
   for (long long i = z; i < n; i += Z) dst[i] = src[i];
 }
+
+// Edges of a check handled together: their loads are issued before their updates.  The
+// edges of one check touch distinct variables and distinct C2V slots (a predecessor slot
+// lies in another base row), so the loads of a chunk never read what an earlier edge of
+// the chunk writes; the updates keep the ascending (forward) or descending (adjoint) edge
+// order, so every sum is formed in the same order as with one edge at a time.
+constexpr int kGradChunk = 4;
 
 // Forward sweeps t0..t1 (1-based, inclusive) of one frame, optionally recording the tape.
 __device__ void forward_sweeps(const GParams& p, const Shared& sh, const Frame& fr, bool act,
@@ -106,38 +119,57 @@ __device__ void forward_sweeps(const GParams& p, const Shared& sh, const Frame& 
       if (act) {
         float Sacc = 0.0f;
         uint32_t sig = 0;
-        for (int k = sh.rptr[r]; k < sh.rptr[r + 1]; ++k) {
-          const BaseEdge be = sh.e[k];
-          const int zv = mod_add(z + be.s, Z);
-          const int v = be.c * Z + zv;
-          const bool self = be.flags & kSelf;
-          const float q = fr.Q[v];
-          float Rn = 0.0f, d = 0.0f, smag = 0.0f;
-          if (!(t == 1 && (be.flags & kFirst))) {
-            int zj = zv - be.ps;
-            zj = zj < 0 ? zj + Z : zj;
-            const float Sj = fr.S[be.pr * Z + zj];
-            d = __fsub_rn(fabsf(Sj), fr.P[v]);
-            const float mag = phi_eval(fabsf(d), p.phi_xlo, sh.tab);
-            const int tau = (be.pr < r) ? t : t - 1;
-            const float wm = __fmul_rn(p.w[(tau - 1) * p.mb + be.pr], mag);
-            const bool neg = sign_bit(Sj) ^ (q < 0.0f);
-            Rn = neg ? -wm : wm;
-            smag = neg ? -mag : mag;
-            if (!self) fr.R[be.pe * Z + zj] = Rn;
+        const int k1 = sh.rptr[r + 1];
+        for (int kb = sh.rptr[r]; kb < k1; kb += kGradChunk) {
+          float q[kGradChunk], pv[kGradChunk], sj[kGradChunk], ro[kGradChunk];
+          int vv[kGradChunk], zjj[kGradChunk];
+#pragma unroll
+          for (int j = 0; j < kGradChunk; ++j) {
+            const int k = kb + j;
+            if (k < k1) {
+              const BaseEdge be = sh.e[k];
+              const int zv = mod_add(z + be.s, Z);
+              int zj = zv - be.ps;
+              zj = zj < 0 ? zj + Z : zj;
+              vv[j] = be.c * Z + zv;
+              zjj[j] = zj;
+              q[j] = fr.Q[vv[j]];
+              pv[j] = fr.P[vv[j]];
+              sj[j] = fr.S[be.pr * Z + zj];
+              ro[j] = (!(be.flags & kSelf) && t > 1) ? fr.R[k * Z + z] : 0.0f;
+            }
           }
-          const float rold = self ? Rn : (t > 1 ? fr.R[k * Z + z] : 0.0f);
-          const float qn = __fsub_rn(__fadd_rn(q, Rn), rold);
-          const float phn = phi_eval(fabsf(qn), p.phi_xlo, sh.tab);
-          Sacc = __fadd_rn(Sacc, phn);
-          sig ^= (qn < 0.0f);
-          fr.Q[v] = qn;
-          fr.P[v] = phn;
-          if (tape) {
-            const long long o = static_cast<long long>(ts) * p.E + k * Z + z;
-            fr.td[o] = d;
-            fr.tm[o] = smag;
-            fr.tq[o] = qn;
+#pragma unroll
+          for (int j = 0; j < kGradChunk; ++j) {
+            const int k = kb + j;
+            if (k < k1) {
+              const BaseEdge be = sh.e[k];
+              const bool self = be.flags & kSelf;
+              float Rn = 0.0f, d = 0.0f, smag = 0.0f;
+              if (!(t == 1 && (be.flags & kFirst))) {
+                d = __fsub_rn(fabsf(sj[j]), pv[j]);
+                const float mag = phi_eval(fabsf(d), p.phi_xlo, sh.tab);
+                const int tau = (be.pr < r) ? t : t - 1;
+                const float wm = __fmul_rn(sh.w[(tau - 1) * p.mb + be.pr], mag);
+                const bool neg = sign_bit(sj[j]) ^ (q[j] < 0.0f);
+                Rn = neg ? -wm : wm;
+                smag = neg ? -mag : mag;
+                if (!self) fr.R[be.pe * Z + zjj[j]] = Rn;
+              }
+              const float rold = self ? Rn : ro[j];
+              const float qn = __fsub_rn(__fadd_rn(q[j], Rn), rold);
+              const float phn = phi_eval(fabsf(qn), p.phi_xlo, sh.tab);
+              Sacc = __fadd_rn(Sacc, phn);
+              sig ^= (qn < 0.0f);
+              fr.Q[vv[j]] = qn;
+              fr.P[vv[j]] = phn;
+              if (tape) {
+                const long long o = static_cast<long long>(ts) * p.E + k * Z + z;
+                fr.td[o] = d;
+                fr.tm[o] = smag;
+                fr.tq[o] = qn;
+              }
+            }
           }
         }
         fr.S[r * Z + z] = sig ? -Sacc : Sacc;
@@ -189,7 +221,7 @@ __global__ void __launch_bounds__(512) weighted_forward_kernel(const GParams p) 
       const float Sk = fr.S[rk * Z + zk];
       const float q = fr.Q[v];
       const float mag = phi_eval(fabsf(__fsub_rn(fabsf(Sk), fr.P[v])), p.phi_xlo, sh.tab);
-      const float wm = __fmul_rn(p.w[(p.T - 1) * p.mb + rk], mag);
+      const float wm = __fmul_rn(sh.w[(p.T - 1) * p.mb + rk], mag);
       p.soft[frame * p.N + v] = __fadd_rn(q, (sign_bit(Sk) ^ (q < 0.0f)) ? -wm : wm);
     }
   }
@@ -219,7 +251,7 @@ __global__ void __launch_bounds__(512) weighted_backward_kernel(const GParams p)
         const float d = __fsub_rn(fabsf(Sm), fr.P[v]);
         const float mag = phi_eval(fabsf(d), xlo, sh.tab);
         const float sgn = (sign_bit(Sm) ^ (q < 0.0f)) ? -1.0f : 1.0f;
-        const float w = p.w[(p.T - 1) * p.mb + r];
+        const float w = sh.w[(p.T - 1) * p.mb + r];
         const float gl = p.gsoft[frame * p.N + v];
         fr.gQ[v] = gl;
         gwx = gl * sgn * mag;
@@ -247,41 +279,77 @@ __global__ void __launch_bounds__(512) weighted_backward_kernel(const GParams p)
           gSacc = fr.gS[m];
           fr.gS[m] = 0.0f;
         }
-        for (int k = sh.rptr[r + 1] - 1; k >= sh.rptr[r]; --k) {
-          const BaseEdge be = sh.e[k];
-          const bool first = (t == 1) && (be.flags & kFirst);
-          const int tau = (be.pr < r) ? t : t - 1;
-          float gwx = 0.0f;
-          if (act) {
-            const int zv = mod_add(z + be.s, Z);
-            const int v = be.c * Z + zv;
-            const bool self = be.flags & kSelf;
-            const long long o = static_cast<long long>(ts) * p.E + k * Z + z;
-            const float d = fr.td[o], smag = fr.tm[o], qn = fr.tq[o];
-            // phn = phi(|qn|) feeds phi_v and the sum S of this check
-            const float gphn = fr.gP[v] + gSacc;
-            const float gqn = fr.gQ[v] + gphn * phi_deriv(fabsf(qn), xlo, sh.tab) *
-                                             (qn < 0.0f ? -1.0f : 1.0f);
-            fr.gR[k * Z + z] -= gqn;  // qn = (Q + Rn) - R[own]
-            float gRn = gqn;           // and Lambda = Q + Rn
-            fr.gQ[v] = gqn;
-            fr.gP[v] = 0.0f;
-            if (!first) {
+        const int k0 = sh.rptr[r];
+        for (int kb = sh.rptr[r + 1] - 1; kb >= k0; kb -= kGradChunk) {
+          // loads of the chunk (edges kb, kb - 1, ...): the tape, the adjoints of the
+          // variables and of the edge's own and predecessor C2V slots
+          float td[kGradChunk], tm[kGradChunk], tq[kGradChunk], gpv[kGradChunk],
+              gqv[kGradChunk], gro[kGradChunk], grs[kGradChunk];
+          int vv[kGradChunk], zjj[kGradChunk];
+#pragma unroll
+          for (int j = 0; j < kGradChunk; ++j) {
+            const int k = kb - j;
+            if (act && k >= k0) {
+              const BaseEdge be = sh.e[k];
+              const int zv = mod_add(z + be.s, Z);
               int zj = zv - be.ps;
               zj = zj < 0 ? zj + Z : zj;
-              const int slot = self ? k * Z + z : be.pe * Z + zj;
-              gRn += fr.gR[slot];      // R[slot] = Rn
-              fr.gR[slot] = 0.0f;
-              gwx = gRn * smag;        // Rn = sgn * w * mag
-              const float w = p.w[(tau - 1) * p.mb + be.pr];
-              const float sgn = smag < 0.0f ? -1.0f : 1.0f;
-              const float gd = gRn * sgn * w * phi_deriv(fabsf(d), xlo, sh.tab) *
-                               (d < 0.0f ? -1.0f : 1.0f);
-              atomicAdd(fr.gS + be.pr * Z + zj, gd);  // d = |S_cj| - phi_v
-              fr.gP[v] = -gd;
+              vv[j] = be.c * Z + zv;
+              zjj[j] = zj;
+              const long long o = static_cast<long long>(ts) * p.E + k * Z + z;
+              td[j] = fr.td[o];
+              tm[j] = fr.tm[o];
+              tq[j] = fr.tq[o];
+              gpv[j] = fr.gP[vv[j]];
+              gqv[j] = fr.gQ[vv[j]];
+              gro[j] = fr.gR[k * Z + z];
+              // a weight-1 edge is its own predecessor: its slot is read after the update
+              grs[j] = (be.flags & kSelf) ? 0.0f : fr.gR[be.pe * Z + zj];
             }
           }
-          if (!first) add_gw(sh, (tau - 1) * p.mb + be.pr, gwx);
+#pragma unroll
+          for (int j = 0; j < kGradChunk; ++j) {
+            const int k = kb - j;
+            if (k < k0) continue;  // uniform: the same edges for every lane
+            const BaseEdge be = sh.e[k];
+            const bool first = (t == 1) && (be.flags & kFirst);
+            const int tau = (be.pr < r) ? t : t - 1;
+            float gwx = 0.0f;
+            if (act) {
+              const int v = vv[j];
+              const bool self = be.flags & kSelf;
+              const float d = td[j], smag = tm[j], qn = tq[j];
+              // phn = phi(|qn|) feeds phi_v and the sum S of this check
+              const float gphn = gpv[j] + gSacc;
+              const float gqn = gqv[j] + gphn * phi_deriv(fabsf(qn), xlo, sh.tab) *
+                                             (qn < 0.0f ? -1.0f : 1.0f);
+              const float gown = gro[j] - gqn;  // qn = (Q + Rn) - R[own]
+              float gRn = gqn;                   // and Lambda = Q + Rn
+              fr.gQ[v] = gqn;
+              float gpn = 0.0f;
+              if (first) {
+                fr.gR[k * Z + z] = gown;
+              } else {
+                // R[slot] = Rn; the slot of a weight-1 edge is its own
+                gRn += self ? gown : grs[j];
+                if (self) {
+                  fr.gR[k * Z + z] = 0.0f;
+                } else {
+                  fr.gR[k * Z + z] = gown;
+                  fr.gR[be.pe * Z + zjj[j]] = 0.0f;
+                }
+                gwx = gRn * smag;  // Rn = sgn * w * mag
+                const float w = sh.w[(tau - 1) * p.mb + be.pr];
+                const float sgn = smag < 0.0f ? -1.0f : 1.0f;
+                const float gd = gRn * sgn * w * phi_deriv(fabsf(d), xlo, sh.tab) *
+                                 (d < 0.0f ? -1.0f : 1.0f);
+                atomicAdd(fr.gS + be.pr * Z + zjj[j], gd);  // d = |S_cj| - phi_v
+                gpn = -gd;
+              }
+              fr.gP[v] = gpn;
+            }
+            if (!first) add_gw(sh, (tau - 1) * p.mb + be.pr, gwx);
+          }
         }
         __syncthreads();
       }

@@ -859,7 +859,7 @@ int grad_setup(const cbp_code_t* c, int batch, int T, int ckpt, GParams* p, int*
   *ws_bytes = ff * sizeof(float) * static_cast<size_t>(batch);
   const size_t sm = sizeof(float4) * kPhiSegments + sizeof(BaseEdge) * c->nnzb +
                     sizeof(int) * ((c->mb + 1 + 3) & ~3) + sizeof(uint2) * ((c->nb + 1) & ~1) +
-                    sizeof(float) * static_cast<size_t>(T) * c->mb;
+                    2 * sizeof(float) * static_cast<size_t>(T) * c->mb;  // gradients, weights
   if (sm > static_cast<size_t>(di->smem_optin)) return CBP_EUNSUPPORTED;
   const int F = std::max(1, 256 / c->Z);
   *threads = (F * c->Z + 31) / 32 * 32;
