@@ -107,7 +107,8 @@ __device__ __forceinline__ void copy_state(float* dst, const float* src, long lo
 // lies in another base row), so the loads of a chunk never read what an earlier edge of
 // the chunk writes; the updates keep the ascending (forward) or descending (adjoint) edge
 // order, so every sum is formed in the same order as with one edge at a time.
-constexpr int kGradChunk = 4;
+constexpr int kGradChunk = 4;     // forward sweeps
+constexpr int kGradChunkAdj = 3;  // adjoint sweeps (94 registers: 3 CTAs of 192 per SM)
 
 // Forward sweeps t0..t1 (1-based, inclusive) of one frame, optionally recording the tape.
 __device__ void forward_sweeps(const GParams& p, const Shared& sh, const Frame& fr, bool act,
@@ -280,14 +281,14 @@ __global__ void __launch_bounds__(512) weighted_backward_kernel(const GParams p)
           fr.gS[m] = 0.0f;
         }
         const int k0 = sh.rptr[r];
-        for (int kb = sh.rptr[r + 1] - 1; kb >= k0; kb -= kGradChunk) {
+        for (int kb = sh.rptr[r + 1] - 1; kb >= k0; kb -= kGradChunkAdj) {
           // loads of the chunk (edges kb, kb - 1, ...): the tape, the adjoints of the
           // variables and of the edge's own and predecessor C2V slots
-          float td[kGradChunk], tm[kGradChunk], tq[kGradChunk], gpv[kGradChunk],
-              gqv[kGradChunk], gro[kGradChunk], grs[kGradChunk];
-          int vv[kGradChunk], zjj[kGradChunk];
+          float td[kGradChunkAdj], tm[kGradChunkAdj], tq[kGradChunkAdj], gpv[kGradChunkAdj],
+              gqv[kGradChunkAdj], gro[kGradChunkAdj], grs[kGradChunkAdj];
+          int vv[kGradChunkAdj], zjj[kGradChunkAdj];
 #pragma unroll
-          for (int j = 0; j < kGradChunk; ++j) {
+          for (int j = 0; j < kGradChunkAdj; ++j) {
             const int k = kb - j;
             if (act && k >= k0) {
               const BaseEdge be = sh.e[k];
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(512) weighted_backward_kernel(const GParams p)
             }
           }
 #pragma unroll
-          for (int j = 0; j < kGradChunk; ++j) {
+          for (int j = 0; j < kGradChunkAdj; ++j) {
             const int k = kb - j;
             if (k < k0) continue;  // uniform: the same edges for every lane
             const BaseEdge be = sh.e[k];
