@@ -200,6 +200,9 @@ def test_error_paths(code576):
     with pytest.raises(cbp.CbpError):
         bigc.workspace_bytes(4, alg="lbp_nms")
     assert bigc.workspace_bytes(4, alg="cbp_sp") > 0     # CBP has no per-row pool limit
+    with pytest.raises(cbp.CbpError) as e:               # one lane per thread: Z <= 1024
+        cbp.Code(qc.base.clip(max=0), 1025)
+    assert e.value.status == -4
 
 
 def test_wide_rows_cbp_only():
@@ -372,10 +375,11 @@ def test_weight1_column_not_last_in_its_row(monkeypatch, pos, chk, fpt):
     assert_parity(run_gpu(code, fr.llr, "cbp_sp", max_iter=25), ref, f"weight-1 column at {pos}")
 
 
-@pytest.mark.parametrize("Z", [512, 1000])
+@pytest.mark.parametrize("Z", [512, 1000, 1024])
 def test_lifts_above_384(Z):
     # Z = 512: one lane group in a 768-thread CTA (idle lanes, one CTA-wide team);
-    # Z = 1000: only the 1024-thread instance fits, and Z is off the warp grid
+    # Z = 1000: only the 1024-thread instance fits, and Z is off the warp grid;
+    # Z = 1024: the largest lifting the library takes (every thread of the CTA a lane)
     qc = I.relift(I.code_576(), 24)
     qc = I.QCCode(qc.base, Z)             # same shifts (all < 24), lifted by Z
     code = cbp.Code.from_qc(qc)
