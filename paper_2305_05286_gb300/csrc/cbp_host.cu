@@ -278,9 +278,9 @@ struct Plan {
   size_t ws_bytes = 0;
 };
 
-// Lane groups per team for the CBP-SP kernel: the smallest number of groups that fills
-// whole warps, if the CTA splits into at most 15 such teams (named barriers 1..15);
-// otherwise the whole CTA is one team.
+// Lane groups per team (CBP-SP and min-sum kernels): the smallest multiple of the
+// groups that fill whole warps which splits the CTA into 2..15 equal teams (named
+// barriers 1..15); otherwise the whole CTA is one team.
 int team_groups_for(int Z, int groups) {
   int a = Z, b = 32;
   while (b) {
@@ -288,8 +288,8 @@ int team_groups_for(int Z, int groups) {
     a = b;
     b = r;
   }
-  const int tg = 32 / a;
-  if (groups % tg == 0 && groups / tg <= 15 && groups / tg >= 2) return tg;
+  for (int tg = 32 / a; tg <= groups / 2; tg += 32 / a)
+    if (groups % tg == 0 && groups / tg <= 15) return tg;
   return groups;
 }
 
