@@ -164,7 +164,9 @@ int cbp_decode_host(const cbp_code_t* code, const float* llr_host, uint32_t* har
  *   info[6] CTAs launched               info[7] lane groups per synchronising team
  *   info[8] dynamic shared bytes per CTA
  *   info[9] 1 if the CBP-SP instance for codes whose weight-1 edges end their rows runs
- *   info[10], info[11] reserved (0)
+ *   info[10] 1 if the frame-parallel CBP-SP kernel runs (one frame per thread; chosen for
+ *            lifting sizes Z <= 8)
+ *   info[11] reserved (0)
  * `info` is a host array of 12 ints.  Nothing is launched. */
 int cbp_launch_info(const cbp_code_t* code, int batch, const cbp_opts_t* opts, int* info);
 

@@ -111,6 +111,7 @@ int device_init(int dev, DeviceInfo** out) {
                            {ALG_CBP_SP, false, 1, false, true},
                            {ALG_CBP_SP, true, 1, false, false, true},
                            {ALG_CBP_SP, false, 1, false, false, true},
+                           {ALG_CBP_SP, false, 1, false, false, false, true},
                            {ALG_CBP_NMS, true, 1}, {ALG_CBP_NMS, false, 1},
                            {ALG_LBP_NMS, false, 1}, {ALG_FBP_SP, false, 1}};
     for (const Variant& v : all)
@@ -276,7 +277,51 @@ struct Plan {
   WsLayout ws{};
   int sh_frame = 0;
   size_t ws_bytes = 0;
+  // frame-parallel kernel (v.fp): slots and workspace offsets, see KParams
+  long long fp_slots = 0, fp_off_sv = 0, fp_off_s = 0, fp_off_r = 0, fp_off_b = 0;
 };
+
+// CBP-SP takes the frame-parallel kernel when the lane-parallel plan keeps fewer lanes
+// than this busy per SM (small Z with large per-frame shared state, e.g. Z = 1 codes), or
+// when no frame fits its shared memory.
+constexpr int kFpMinLanes = 128;
+
+// Launch plan of the frame-parallel CBP-SP kernel: one frame slot per thread, as many
+// CTAs as the SMs hold (fewer for small batches); the workspace holds each array of
+// every slot element-major, slot innermost, each array 256-byte aligned.
+int make_fp_plan(const cbp_code* c, const DeviceInfo& di, int batch, Plan* out) {
+  Plan pl;
+  pl.v = Variant{ALG_CBP_SP, false, 1};
+  pl.v.fp = true;
+  pl.threads = fp_threads();
+  pl.smem = sizeof(float4) * kPhiSegments + sizeof(int) * align4(c->mb + 1) +
+            sizeof(uint2) * ((c->nb + 1) & ~1);
+  if (pl.smem > static_cast<size_t>(di.smem_optin)) return CBP_EUNSUPPORTED;
+  int ctas = 0;
+  if (decoder_occupancy(pl.v, pl.threads, pl.smem, &ctas) != cudaSuccess) return CBP_ECUDA;
+  if (ctas < 1) return CBP_EUNSUPPORTED;
+  const long long need = (static_cast<long long>(batch) + pl.threads - 1) / pl.threads;
+  pl.grid = static_cast<int>(std::max(1LL, std::min<long long>(need, 1LL * di.sms * ctas)));
+  pl.F = pl.threads;
+  pl.team_groups = 1;
+  pl.ctas_per_sm = ctas;
+  pl.frames_per_sm = ctas * pl.threads;
+  pl.fp_slots = static_cast<long long>(pl.grid) * pl.threads;
+  long long off = 0;
+  auto take = [&](long long elems) {
+    const long long o = off;
+    off += static_cast<long long>(align64(static_cast<size_t>(elems * pl.fp_slots)));
+    return o;
+  };
+  take(2LL * c->ncomp * c->Z);  // QP at offset 0
+  pl.fp_off_sv = take(2LL * c->nself * c->Z);
+  pl.fp_off_s = take(c->M);
+  pl.fp_off_r = take(c->E);
+  pl.fp_off_b = take((c->N + 31) / 32);
+  pl.ws_bytes = static_cast<size_t>(off) * sizeof(float);
+  *out = pl;
+  return CBP_OK;
+}
 
 // Lane groups per team (CBP-SP and min-sum kernels): the smallest multiple of the
 // groups that fill whole warps which splits the CTA into 2..15 equal teams (named
@@ -297,8 +342,8 @@ int team_groups_for(int Z, int groups) {
 // most resident frames per SM (ties: more resident warps); the variant with the most
 // resident frames wins (ties: the earlier one in the candidate list).  CBP_PLAN_CHK=0/1
 // and CBP_PLAN_FPT=1/2 in the environment restrict the candidates (tuning experiments).
-int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan* out,
-              int stop = CBP_STOP_SYNDROME) {
+int make_lane_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan* out,
+                   int stop) {
   std::vector<Variant> cands;
   switch (alg) {
     case ALG_CBP_SP:
@@ -395,6 +440,23 @@ int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan*
   return CBP_OK;
 }
 
+// Launch plan of a decode: the lane-parallel kernels, or for CBP-SP the frame-parallel one
+// where the lane-parallel plan would leave the SMs' lanes idle (CBP_PLAN_FP=0/1 in the
+// environment forces either; the paper-literal stop and the no-alloc entry point always
+// run lane-parallel).
+int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan* out,
+              int stop = CBP_STOP_SYNDROME, bool allow_fp = true) {
+  const bool sp = alg == ALG_CBP_SP && stop != CBP_STOP_WINDOW && allow_fp;
+  const char* e = sp ? std::getenv("CBP_PLAN_FP") : nullptr;
+  if (e && e[0] == '1') return make_fp_plan(c, di, batch, out);
+  const int rc = make_lane_plan(c, di, alg, batch, out, stop);
+  if (!sp || (e && e[0] == '0')) return rc;
+  if (rc == CBP_EUNSUPPORTED ||
+      (rc == CBP_OK && 1LL * out->frames_per_sm * c->Z < kFpMinLanes))
+    return make_fp_plan(c, di, batch, out);
+  return rc;
+}
+
 // Kernel parameters of one code under a plan (buffers are filled in by the caller).
 KParams code_params(const cbp_code* c, const DeviceInfo& di, const Plan& pl, int batch,
                     int max_iter, int stop, float alpha) {
@@ -431,6 +493,11 @@ KParams code_params(const cbp_code* c, const DeviceInfo& di, const Plan& pl, int
   p.ws_off_c = pl.ws.off_c;
   p.ws_cta = static_cast<long long>(pl.F) * pl.ws.slot;
   p.sh_frame = pl.sh_frame;
+  p.fp_slots = pl.fp_slots;
+  p.fp_off_sv = pl.fp_off_sv;
+  p.fp_off_s = pl.fp_off_s;
+  p.fp_off_r = pl.fp_off_r;
+  p.fp_off_b = pl.fp_off_b;
   return p;
 }
 
@@ -656,7 +723,7 @@ int cbp_launch_info(const cbp_code_t* c, int batch, const cbp_opts_t* opts, int*
   info[7] = pl.team_groups;
   info[8] = static_cast<int>(pl.smem);
   info[9] = pl.v.self_last ? 1 : 0;
-  info[10] = 0;
+  info[10] = pl.v.fp ? 1 : 0;
   info[11] = 0;
   return CBP_OK;
 }
@@ -991,7 +1058,7 @@ int cbp_decode_noalloc(const cbp_code_t* c, const float* llr, uint32_t* hard_out
   void* scratch = nullptr;
   if (int rc = noalloc_scratch(dev, &scratch)) return rc;
   Plan pl;
-  if (int rc = make_plan(c, *di, ALG_CBP_SP, batch, &pl)) return rc;
+  if (int rc = make_plan(c, *di, ALG_CBP_SP, batch, &pl, CBP_STOP_SYNDROME, false)) return rc;
   // Fit the launch into the array: fewer CTAs, and if one CTA is still too big, fewer
   // frame slots per CTA.  Slots loop over frames, so any grid decodes the whole batch.
   const size_t cap = CBP_NOALLOC_SCRATCH_BYTES;

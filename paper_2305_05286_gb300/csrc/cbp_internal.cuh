@@ -150,6 +150,9 @@ struct KParams {
   long long ws_off_s;    // CBP-SP: check-beliefs when not shared; min-sum: check state
   long long ws_off_c;    // CBP min-sum: (min1, min2) per check when not shared
   int sh_frame;          // floats of shared memory per lane group
+  // frame-parallel CBP-SP (cbp_fp.cu): frame slots of the launch (one per thread) and the
+  // offsets (floats) of SV, S, R and the decision bits in the workspace; QP is at 0
+  long long fp_slots, fp_off_sv, fp_off_s, fp_off_r, fp_off_b;
 };
 
 // Several codes in one launch (CBP-SP): per-code parameters and the chunk list.
@@ -179,6 +182,7 @@ struct Variant {
   bool wide = false;  // CBP-SP: instance that allows 1024 threads per CTA (Z > 512)
   bool win = false;   // CBP-SP with the paper-literal stop (CBP_STOP_WINDOW)
   bool self_last = false;  // CBP-SP, one frame per group: every weight-1 edge ends its row
+  bool fp = false;         // CBP-SP, frame-parallel kernel: one frame per thread
 };
 
 // Sizes that fix the shared-memory and workspace layout of a launch.
@@ -205,6 +209,8 @@ void* sp_win_kernel_ptr(bool chk_shared);                   // cbp_sp.cu
 cudaError_t launch_multi(bool chk_shared, int fpt, bool self_last, const MultiParams& mp, int grid,
                          int threads, size_t smem, cudaStream_t st);
 void* minsum_kernel_ptr(int alg, bool chk_shared);          // cbp_minsum.cu
+void* fp_kernel_ptr();                                       // cbp_fp.cu
+int fp_threads();                                            // cbp_fp.cu: threads per CTA
 void* flood_kernel_ptr();              // cbp_flood.cu
 cudaError_t launch_phi(const float* x, float* y, long long n, const float4* tab, float xlo,
                        cudaStream_t st);

@@ -428,3 +428,63 @@ def test_decode_host_with_the_window_stop(code576):
                             chunk=64)
     assert np.array_equal(i.numpy(), ref["iters"])
     assert np.array_equal(cbp.unpack_bits(h, code.N).numpy(), ref["hard"])
+
+
+FP_CASES = [("576", 2000, 2.0, "syndrome"), ("576", 257, 1.5, "none"), ("2304", 300, 1.75, "syndrome"),
+            ("z4", 1000, 2.5, "syndrome"), ("z1", 333, 2.5, "syndrome"), ("peg", 700, 2.0, "syndrome")]
+
+
+@pytest.mark.parametrize("name,batch,ebn0,stop", FP_CASES)
+def test_frame_parallel_kernel(monkeypatch, name, batch, ebn0, stop):
+    # One frame per thread, the whole sequential schedule per thread, state element-major
+    # with the frame slot innermost.  The planner picks it where the lane-parallel plan
+    # would keep few lanes busy (the Z = 1 PEG code); elsewhere it is forced on.  Bit for
+    # bit against the oracle, soft output too.
+    qc = {"576": I.code_576, "2304": I.code_2304, "peg": I.code_peg_2048,
+          "z4": lambda: I.relift(I.code_576(), 4), "z1": lambda: I.relift(I.code_576(), 1)}[name]()
+    code = cbp.Code.from_qc(qc)
+    if name == "peg":
+        assert code.launch_info(batch)["frame_parallel"] == 1
+        monkeypatch.setenv("CBP_PLAN_FP", "0")
+        assert code.launch_info(batch)["frame_parallel"] == 0
+    else:
+        assert code.launch_info(batch)["frame_parallel"] == 0
+    monkeypatch.setenv("CBP_PLAN_FP", "1")
+    info = code.launch_info(batch)
+    assert info["frame_parallel"] == 1 and info["threads_per_cta"] == 256
+    fr = I.make_frames(qc, batch, ebn0, seed=4700 + batch, encoder="gf2" if qc.N <= 4096 else "tri")
+    ref = O.OracleCode(qc.base, qc.Z).decode(fr.llr, alg="cbp_sp", max_iter=20, stop=stop,
+                                             threads=THREADS)
+    assert_parity(run_gpu(code, fr.llr, "cbp_sp", max_iter=20, stop=stop), ref, f"{name} fp")
+    assert (ref["iters"] > 0).any()
+
+
+def test_frame_parallel_kernel_on_the_26112_code(large, monkeypatch):
+    # a large lifting through the frame-parallel kernel: each thread walks all 384 lanes of
+    # every base row; a batch of 40 frames leaves most of the launch's slots idle
+    qc, code, oc = large
+    monkeypatch.setenv("CBP_PLAN_FP", "1")
+    assert code.launch_info(40)["frame_parallel"] == 1
+    llr, _ = I.make_frames_torch(qc, 40, 1.0, seed=2300)
+    ref = oc.decode(llr.cpu().numpy(), alg="cbp_sp", max_iter=12, threads=THREADS)
+    assert_parity(run_gpu(code, llr.cpu().numpy(), "cbp_sp", max_iter=12), ref, "26112 fp")
+    monkeypatch.setenv("CBP_PLAN_FP", "0")
+    assert code.launch_info(40)["frame_parallel"] == 0
+
+
+def test_frame_parallel_host_decode_and_status(monkeypatch):
+    # the host-buffer entry point and the non-finite-LLR status through the same kernel
+    qc = I.relift(I.code_576(), 4)
+    code = cbp.Code.from_qc(qc)
+    monkeypatch.setenv("CBP_PLAN_FP", "1")
+    fr = I.make_frames(qc, 700, 2.0, seed=4800)
+    host = torch.from_numpy(fr.llr).pin_memory()
+    h_ref, i_ref, _ = code.decode(host.cuda(), max_iter=20)
+    h, i = code.decode_host(host, max_iter=20, chunk=256)
+    assert torch.equal(i, i_ref.cpu()) and torch.equal(h, h_ref.cpu())
+    code.device_status()
+    bad = fr.llr.copy()
+    bad[5, 7] = np.nan
+    code.decode(torch.from_numpy(bad).cuda(), max_iter=5)
+    torch.cuda.synchronize()
+    assert code.device_status() == cbp.STATUS_NONFINITE_LLR
