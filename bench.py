@@ -206,13 +206,28 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# --code: the decoded code (the throughput workload is the 26112-bit one)
+CODES = {"26112": ("code_26112", "QC-LDPC 46x68 base, Z=384"),
+         "2304": ("code_2304", "QC-LDPC 12x24 base, Z=96"),
+         "576": ("code_576", "QC-LDPC 12x24 base, Z=24"),
+         "peg2048": ("code_peg_2048", "regular (3,6) PEG code, Z=1")}
+
+
+def bench_code(I, name):
+    return getattr(I, CODES[name][0])()
+
+
 def workload_config(args, qc, note=None):
-    c = {"workload": f"QC-LDPC 46x68 base, Z=384 (N={qc.N}, K={(qc.nb - qc.mb) * qc.Z}), "
+    gb = 4.0 * qc.N * args.frames / 1e9
+    c = {"workload": f"{CODES[getattr(args, 'code', '26112')][1]} (N={qc.N}, "
+                     f"K={(qc.nb - qc.mb) * qc.Z}), "
                      f"{args.frames} BPSK/AWGN frames per launch at Eb/N0 {args.ebn0} dB, "
                      f"max {MAX_ITER} sweeps, syndrome stop",
          "alg": args.alg, "frames_per_launch": args.frames, "ebn0_db": args.ebn0,
          "max_iter": MAX_ITER, "parallelism": "replicas" if args.gpus > 1 else "single",
-         "l2": "inputs larger than L2 (LLRs 4*N bytes per frame, 6.85 GB per launch)"}
+         "l2": (f"inputs larger than L2 (LLRs 4*N bytes per frame, {gb:.2f} GB per launch)"
+                if gb > 0.129 else f"LLRs {gb * 1e3:.0f} MB per launch, within L2 "
+                                   "(each step decodes the same frames)")}
     if note:
         c["note"] = note
     return c
@@ -244,11 +259,12 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
     stream = torch.cuda.current_stream(dev)
-    qc = I.code_26112()
+    qc = bench_code(I, args.code)
     K = (qc.nb - qc.mb) * qc.Z
     code = cbp.Code.from_qc(qc)
     B = args.frames
-    llr, cw = I.make_frames_torch(qc, B, args.ebn0, seed=frame_seed(rank), device=dev)
+    llr, cw = I.make_frames_torch(qc, B, args.ebn0, seed=frame_seed(rank), device=dev,
+                                  zero_codeword=not I.is_lower_triangular(qc))
     hard = torch.empty((B, code.words), dtype=torch.int32, device=dev)
     iters = torch.empty((B,), dtype=torch.int32, device=dev)
     ws = code.workspace(B, args.alg)
@@ -280,7 +296,7 @@ def run_ours(args, rank, world, dist):
     ops = alu_ops(args.alg, qc, st["sweeps_total"])
     achieved = ops / (ms / 1e3) / 1e12
     traffic, traffic_src = args.traffic, "--traffic"
-    if traffic is None and args.alg in TRAFFIC_PER_FRAME_SWEEP:
+    if traffic is None and args.alg in TRAFFIC_PER_FRAME_SWEEP and args.code == "26112":
         frame_sweeps = st["sweeps_total"]
         traffic = TRAFFIC_PER_FRAME_SWEEP[args.alg] * frame_sweeps
         traffic_src = TRAFFIC_SOURCE
@@ -677,6 +693,8 @@ def main():
     ap.add_argument("--alpha", type=float, default=0.75,
                     help="min-sum normalisation for --sweep (the bench line uses 0.75)")
     ap.add_argument("--learned", action="store_true")
+    ap.add_argument("--code", choices=sorted(CODES), default="26112",
+                    help="decoded code of the throughput run (default: the 26112-bit workload)")
     ap.add_argument("--multi", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="--multi: skip the autotuner and use the library's default options")
