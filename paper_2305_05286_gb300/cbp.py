@@ -218,16 +218,27 @@ class Code:
         iters int32 [B], soft float32 [B, N] or None).
 
         A CPU ``llr`` is copied to the device first and the results are copied back
-        (the end-to-end path); a CUDA ``llr`` stays on the device."""
+        (the end-to-end path); a CUDA ``llr`` stays on the device.  With ``stream`` the
+        decoding runs there, ordered after the current stream's work.  The code's cached
+        workspace serves every call, so calls that may overlap on different streams should
+        use ``decode_into`` with a workspace each."""
         host = not llr.is_cuda
         dev = torch.device(f"cuda:{self.device}")
+        cur = torch.cuda.current_stream(dev)
+        other = stream is not None and stream != cur  # copies on `cur`, decoding on `stream`
         x = llr.to(dev, non_blocking=True) if host else llr
         x = x.contiguous()
         B = x.shape[0]
         hard = torch.empty((B, self.words), dtype=torch.int32, device=dev)
         iters = torch.empty((B,), dtype=torch.int32, device=dev)
         sb = torch.empty((B, self.N), dtype=torch.float32, device=dev) if soft else None
+        if other:
+            stream.wait_stream(cur)
+            for t in (x, hard, iters) + ((sb,) if sb is not None else ()):
+                t.record_stream(stream)  # not reused by the allocator before `stream` is done
         self.decode_into(x, hard, iters, max_iter, alg, alpha, stop, sb, stream=stream)
+        if host and other:
+            cur.wait_stream(stream)
         if host:
             pin = llr.is_pinned()
             hard_h = torch.empty(hard.shape, dtype=hard.dtype, pin_memory=pin)

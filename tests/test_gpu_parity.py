@@ -420,6 +420,22 @@ def test_concurrent_streams_and_host_threads(code576):
         assert np.array_equal(cbp.unpack_bits(h, code.N).cpu().numpy(), rh)
 
 
+def test_decode_from_host_memory_on_another_stream(code576):
+    # the copy runs on the current stream and the decoding on `stream`: the decoding must
+    # wait for the copy, and the results must wait for the decoding
+    qc, code, _ = code576
+    fr = I.make_frames(qc, 3000, 2.0, seed=7300)
+    ref = run_gpu(code, fr.llr, "cbp_sp")
+    s = torch.cuda.Stream()
+    for pinned in (True, False):
+        host = torch.from_numpy(fr.llr)
+        host = host.pin_memory() if pinned else host
+        h, it, _ = code.decode(host, max_iter=30, stream=s)
+        torch.cuda.synchronize()
+        assert not h.is_cuda and np.array_equal(it.numpy(), ref[1])
+        assert np.array_equal(cbp.unpack_bits(h, code.N).numpy(), ref[0])
+
+
 def test_decode_host_with_the_window_stop(code576):
     qc, code, oc = code576
     fr = I.make_frames(qc, 250, 3.0, seed=7100)
