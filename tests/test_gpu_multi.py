@@ -234,6 +234,16 @@ def test_multi_weight1_last_instance_choice(mixed):
     assert np.array_equal(got[7][1], ref["iters"]) and np.array_equal(got[7][0], ref["hard"])
 
 
+def test_small_liftings_split_into_teams(mixed):
+    # lane groups synchronise per base row only within their team; Z = 16 and Z = 32 CTAs
+    # (48 and 24 groups) split into 12 teams of whole warps, Z = 384 into one per frame
+    qcs, codes = mixed
+    for c, groups, team in ((codes[0], 48, 4), (codes[1], 24, 2), (codes[7], 2, 1)):
+        info = c.launch_info(20000)
+        assert c.Z * info["team_lane_groups"] % 32 == 0
+        assert (info["lane_groups_per_cta"], info["team_lane_groups"]) == (groups, team), c.Z
+
+
 def test_multi_tail_of_one_round_chunks(mixed):
     # the last tail_percent % of an item's frames (whole rounds) run as one-round chunks
     qcs, codes = mixed
