@@ -165,10 +165,8 @@ __global__ void __launch_bounds__(kFpThreads) cbp_fp_kernel(const KParams p) {
           const int v = vb + j;
           if (v < N) {
             const float mag = phi_eval(fabsf(__fsub_rn(fabsf(sk[j]), qp[j].y)), xlo, tab);
-            const float lb = __fadd_rn(
-                qp[j].x,
-                __uint_as_float(__float_as_uint(mag) |
-                                ((__float_as_uint(sk[j]) ^ __float_as_uint(qp[j].x)) & 0x80000000u)));
+            const uint32_t sg = (__float_as_uint(sk[j]) ^ __float_as_uint(qp[j].x)) & 0x80000000u;
+            const float lb = __fadd_rn(qp[j].x, __uint_as_float(__float_as_uint(mag) | sg));
             if (p.soft) p.soft[frame * N + v] = lb;
             word |= static_cast<uint32_t>(lb < 0.0f) << (v & 31);
             if ((v & 31) == 31 || v == N - 1) {

@@ -4,8 +4,9 @@ The library's default launch shape (one 768-thread CTA per SM, four frame rounds
 chunk, the last 20 % of each item's frames in one-round chunks) is a safe choice, not
 always the fastest: small lifting sizes leave lanes idle, two interleaved frames per
 lane group hide more latency, and the size of chunks and of the one-round tail trade
-per-chunk overhead against idle SMs at the end of the launch.  `tune_multi` times each candidate option
-set on the caller's own frames with CUDA events and returns the fastest.  All
+per-chunk overhead against idle SMs at the end of the launch.  `tune_multi` times each
+candidate option set on the caller's own frames with CUDA events and returns the
+fastest.  All
 decoding runs in libcbp; this module only chooses among its launch options.
 """
 from __future__ import annotations

@@ -446,8 +446,9 @@ def test_decode_host_with_the_window_stop(code576):
     assert np.array_equal(cbp.unpack_bits(h, code.N).numpy(), ref["hard"])
 
 
-FP_CASES = [("576", 2000, 2.0, "syndrome"), ("576", 257, 1.5, "none"), ("2304", 300, 1.75, "syndrome"),
-            ("z4", 1000, 2.5, "syndrome"), ("z1", 333, 2.5, "syndrome"), ("peg", 700, 2.0, "syndrome")]
+FP_CASES = [("576", 2000, 2.0, "syndrome"), ("576", 257, 1.5, "none"),
+            ("2304", 300, 1.75, "syndrome"), ("z4", 1000, 2.5, "syndrome"),
+            ("z1", 333, 2.5, "syndrome"), ("peg", 700, 2.0, "syndrome")]
 
 
 @pytest.mark.parametrize("name,batch,ebn0,stop", FP_CASES)
