@@ -61,3 +61,22 @@ def test_reference_arm_under_torchrun_world_2():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_bench_code_choices_resolve():
+    # every --code name loads a committed code, and the workload line names its sizes
+    import argparse
+
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2305_05286_gb300 import inputs as I
+
+    for name in bench.CODES:
+        qc = bench.bench_code(I, name)
+        args = argparse.Namespace(code=name, frames=1000, ebn0=2.5, alg="cbp_sp", gpus=1)
+        cfg = bench.workload_config(args, qc)
+        assert f"N={qc.N}" in cfg["workload"] and bench.CODES[name][1] in cfg["workload"]
+        assert "within L2" in cfg["l2"] or "larger than L2" in cfg["l2"]
+    qc = bench.bench_code(I, "26112")
+    big = argparse.Namespace(code="26112", frames=65536, ebn0=2.5, alg="cbp_sp", gpus=1)
+    assert "6.85 GB" in bench.workload_config(big, qc)["l2"]
