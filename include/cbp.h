@@ -164,8 +164,9 @@ int cbp_decode_host(const cbp_code_t* code, const float* llr_host, uint32_t* har
  *   info[6] CTAs launched               info[7] lane groups per synchronising team
  *   info[8] dynamic shared bytes per CTA
  *   info[9] 1 if the CBP-SP instance for codes whose weight-1 edges end their rows runs
- *   info[10] 1 if the frame-parallel CBP-SP kernel runs (one frame per thread; chosen for
- *            lifting sizes Z <= 8)
+ *   info[10] 1 if the frame-parallel CBP-SP kernel runs (one frame per thread; chosen when
+ *            the lane-parallel plan would keep fewer than 128 lanes per SM busy, e.g. for
+ *            Z = 1 codes, or cannot place a frame in shared memory)
  *   info[11] reserved (0)
  * `info` is a host array of 12 ints.  Nothing is launched. */
 int cbp_launch_info(const cbp_code_t* code, int batch, const cbp_opts_t* opts, int* info);
