@@ -33,23 +33,27 @@ EBN0_OPERATING = 2.5
 FRAMES = 65536
 MAX_ITER = 20
 
-# Algorithmic issue slots per unit: the minimal instruction mix (FP32/INT32 arithmetic
-# and the memory instructions) of one edge update of one sweep, of the syndrome work
-# per edge and of the end-of-sweep posterior per variable, for each algorithm as
-# defined.  phi: 20 (clamp 2, centre rounding 2, offset 1, k and offset above 2: 3,
-# regime test and selects 3, index 3, table fetch 2, Horner 3).  CBP-SP edge: 64 = B2V
-# 23 (|S| - phi 1, phi 20, sign 2) + V2C 2 + C2B 22 (phi 20, S add 1, sign 1) + memory 5
-# (Q*/phi load and store, S load, R load and store) + lane indexing 12.  Posterior per
-# variable 30 (loads, phi, sign, add, compare, packing).  Min-sum: compare/select chains
-# in place of phi.
-OPS_EDGE = {"cbp_sp": 64, "cbp_nms": 31, "lbp_nms": 28, "fbp_sp": 64}
-OPS_VAR = {"cbp_sp": 30, "cbp_nms": 10, "lbp_nms": 3, "fbp_sp": 5}
-OPS_SYN = 4
-# DRAM bytes (read + write) per frame-sweep of the CBP-SP kernel on the 26112-bit code, from
-# one ncu capture of 2432 frames (14.11 GB over 9699 frame-sweeps); the workspace traffic
-# grows with frame-sweeps, so a launch's traffic is this times its frame-sweeps.
-TRAFFIC_PER_FRAME_SWEEP = {"cbp_sp": 14.11e9 / (2432 * 3.98808)}
-TRAFFIC_SOURCE = "profiles/cbp_sp_kernel_n26112_2432frames.md, scaled by frame-sweeps"
+# Algorithmic operations per unit (the roofline numerator): only the arithmetic the
+# algorithm itself needs, counted in FP32/INT32 lane operations -- no memory
+# instructions, no lane indexing or addressing, no control flow.
+#   phi evaluation: 20 (clamp 2, centre rounding 2, offset 1, k and offset above 2: 3,
+#     regime test and selects 3, index 3, table fetch 2, Horner 3).
+#   CBP-SP edge (Sec. IV-C Step 2; Tables I-II count E sums and E products per sweep):
+#     2 phi + 8 simple operations (|S| - phi, the sign of R^new (2), Q* + R^new,
+#     Lambda - R_old, S += phi, the sign fold, the first-visit select) = 48.
+#   Posterior per variable (Eq. s4e20 read-only, then Eq. s2e7): phi + 4 (|S| - phi,
+#     sign, add, compare) = 24.  Syndrome: 1 XOR per edge.
+#   Min-sum (CBP and layered): about 10 compare/select/add operations per edge in place
+#     of the two phi, 4 per variable.  Flooding BP: the CBP-SP edge count, 4 per variable.
+OPS_EDGE = {"cbp_sp": 48, "cbp_nms": 10, "lbp_nms": 10, "fbp_sp": 48}
+OPS_VAR = {"cbp_sp": 24, "cbp_nms": 4, "lbp_nms": 4, "fbp_sp": 4}
+OPS_SYN = 1
+# ncu counters of the current kernels, taken from one capture each (2432 frames of the
+# 26112-bit code at 2.5 dB): DRAM bytes (read + write) and issued thread-instructions per
+# frame-sweep or edge-sweep.  Each entry names the kernel instance and the capture date,
+# and carries a hash of the kernel sources it was measured on: when the sources change,
+# the numbers are stale and the bench line reports null instead.
+CAPTURES = {}
 
 
 def load_peaks():
@@ -145,6 +149,52 @@ def frame_stats(torch, cbp, qc, hard, iters, cw):
 def alu_ops(alg, qc, sweeps_total):
     per_sweep = qc.E * (OPS_EDGE[alg] + OPS_SYN) + qc.N * OPS_VAR[alg]
     return per_sweep * sweeps_total
+
+
+def kernel_source_hash(alg):
+    """Hash of the kernel sources an algorithm's decoder is compiled from."""
+    import hashlib
+
+    names = ("cbp_minsum.cu" if "nms" in alg else "cbp_flood.cu" if alg == "fbp_sp"
+             else "cbp_sp.cu", "cbp_kernel_common.cuh", "cbp_internal.cuh")
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_2305_05286_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def capture_for(alg, code_name):
+    """The ncu counters of this algorithm's kernel, if they were taken on these sources."""
+    c = CAPTURES.get(alg)
+    if c is None or code_name != "26112" or c["sources"] != kernel_source_hash(alg):
+        return None
+    return c
+
+
+def roofline_entry(alg, qc, st, ms, peak_ops, code_name, traffic_arg):
+    """ALU roofline of one decode: algorithmic operations per second against the issue-rate
+    peak; the kernel's DRAM traffic and issued instructions from its ncu capture."""
+    ops = alu_ops(alg, qc, st["sweeps_total"])
+    achieved = ops / (ms / 1e3) / 1e12
+    cap = capture_for(alg, code_name)
+    traffic, src = traffic_arg, "--traffic"
+    counters = None
+    if traffic is None and cap is not None:
+        traffic = cap["dram_bytes_per_frame_sweep"] * st["sweeps_total"]
+        src = (f"ncu capture of {cap['kernel']} ({cap['date']}, {cap['frames']} frames), "
+               "scaled by frame-sweeps")
+    if traffic is None:
+        src = "no capture of the current kernel sources"
+    if cap is not None:
+        counters = {k: cap[k] for k in ("kernel", "date", "thread_inst_per_edge_sweep",
+                                        "issue_active", "warps_active_per_sm")}
+    return {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "T lane-ops/s",
+            "frac": achieved / peak_ops, "traffic": traffic, "traffic_source": src,
+            "units": {"edge_sweeps": qc.E * st["sweeps_total"],
+                      "var_sweeps": qc.N * st["sweeps_total"],
+                      "ops_per_edge": OPS_EDGE[alg] + OPS_SYN, "ops_per_var": OPS_VAR[alg]},
+            "kernel_counters": counters}
 
 
 def cpu_oracle_rate(qc, llr_host, seconds=12.0, chunk=64):
@@ -293,19 +343,8 @@ def run_ours(args, rank, world, dist):
     sm_mhz = clocks["sm_mhz"] or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1455.0
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_ops = sms * 128 * sm_mhz * 1e6 / 1e12  # T lane-ops/s at the sampled SM clock
-    ops = alu_ops(args.alg, qc, st["sweeps_total"])
-    achieved = ops / (ms / 1e3) / 1e12
-    traffic, traffic_src = args.traffic, "--traffic"
-    if traffic is None and args.alg in TRAFFIC_PER_FRAME_SWEEP and args.code == "26112":
-        frame_sweeps = st["sweeps_total"]
-        traffic = TRAFFIC_PER_FRAME_SWEEP[args.alg] * frame_sweeps
-        traffic_src = TRAFFIC_SOURCE
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "T issue-slots/s",
-                "frac": achieved / peak_ops, "traffic": traffic, "traffic_source": traffic_src,
-                "peak_source": f"{sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (sampled SM clock)",
-                "units": {"edge_sweeps": qc.E * st["sweeps_total"],
-                          "ops_per_edge": OPS_EDGE[args.alg] + OPS_SYN,
-                          "ops_per_var": OPS_VAR[args.alg]}}
+    roofline = roofline_entry(args.alg, qc, st, ms, peak_ops, args.code, args.traffic)
+    roofline["peak_source"] = f"{sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (sampled SM clock)"
     hbm_bytes = B * (4 * qc.N + 4 * code.words + 4)
     roofline["hbm_algorithmic_GBs"] = hbm_bytes / (ms / 1e3) / 1e9
     roofline["hbm_peak_GBs"] = peaks.get("hbm_gbs")
@@ -322,21 +361,29 @@ def run_ours(args, rank, world, dist):
 
     comparators = {}
     if not args.no_comparators:
+        # every comparator is timed like the headline decoder: the same warm-up and timed
+        # steps on the same frames, with its own clock record
         for alg in ("cbp_nms", "lbp_nms", "fbp_sp"):
             if alg == args.alg:
                 continue
             wsa = code.workspace(B, alg)
             f = lambda a=alg, w=wsa: code.decode_into(llr, hard, iters, max_iter=MAX_ITER,
                                                       alg=a, workspace=w)
-            f()
+            for _ in range(args.warmup):
+                f()
             torch.cuda.synchronize()
-            cms = timed_steps(torch, f, 2, stream)
+            with ClockSampler(gpu_identity(torch, local)) as cclk:
+                torch.cuda.synchronize()
+                cms = timed_steps(torch, f, args.steps, stream)
+                torch.cuda.synchronize()
             cs = frame_stats(torch, cbp, qc, hard, iters, cw)
-            c_ops = alu_ops(alg, qc, cs["sweeps_total"]) / (cms / 1e3) / 1e12
+            cro = roofline_entry(alg, qc, cs, cms, peak_ops, args.code, None)
             comparators[alg] = {"gbps": K * B / (cms / 1e3) / 1e9, "ms_per_step": cms,
+                                "steps": args.steps, "warmup": args.warmup,
                                 "fer": cs["fer"], "ber": cs["ber"], "mean_iters": cs["mean_iters"],
-                                "alu_frac": c_ops / peak_ops,
-                                "launch": code.launch_info(B, alg)}
+                                "alu_frac": cro["frac"], "kernel_counters": cro["kernel_counters"],
+                                "clocks": cclk.summary(), "launch": code.launch_info(B, alg)}
+            del wsa
         ws = code.workspace(B, args.alg)
 
     e2e = None
@@ -350,7 +397,8 @@ def run_ours(args, rank, world, dist):
             code.decode_host(host, max_iter=MAX_ITER, alg=args.alg, chunk=args.e2e_chunk,
                              hard=hard_h, iters=iters_h, sync=False)
 
-        e2e_step()
+        for _ in range(args.warmup):
+            e2e_step()
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -601,7 +649,7 @@ def run_multi_bench(args):
             "tune_table": [{"ms": ms, **o} for ms, o in table[:8]],
             "launch": cbp.multi_launch_info(codes, batches, **best),
             "roofline": {"bound": "alu", "achieved": ops / (ms_multi / 1e3) / 1e12, "peak": peak,
-                         "unit": "T issue-slots/s",
+                         "unit": "T lane-ops/s",
                          "frac": ops / (ms_multi / 1e3) / 1e12 / peak},
             "codes": per, "info_bits_per_step": info_bits,
             "config": {"workload": "8 QC codes Z 16..384, rates 1/3..8/9, frames log-uniform "

@@ -219,8 +219,15 @@ int cbp_decode_grad(const cbp_code_t* code, const float* llr, const float* weigh
  * which the library's kernels are loaded holds that array until the process exits.
  * The caller still passes the inputs and outputs (same layout as cbp_decode); the call
  * allocates nothing.
+ *   - It runs the lane-parallel CBP-SP kernel only (never the frame-parallel one that
+ *     cbp_decode picks for codes such as Z = 1 graphs): a code whose frame does not fit
+ *     that kernel's shared memory returns CBP_EUNSUPPORTED, and a small-Z code decodes
+ *     correctly but with few busy lanes.
  *   - Larger batches run with fewer frame slots in flight, so they fit the array; a code
  *     whose single frame slot needs more than the array returns CBP_EWORKSPACE.
+ *   - Errors: CBP_EINVAL (null or misaligned pointers, max_iter < 1, batch < 0),
+ *     CBP_EDEVICE (a code of another device), CBP_EUNSUPPORTED, CBP_EWORKSPACE,
+ *     CBP_ECUDA (the symbol lookup or the launch failed).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
  *   - All calls share the one array and it keeps the previous call's contents (the

@@ -337,8 +337,12 @@ class _WeightedCBP(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, llr, weights, code, T, ckpt_every):
+        if llr.dtype != torch.float32 or not llr.is_cuda or llr.dim() != 2 or llr.shape[1] != code.N:
+            raise ValueError("llr must be a float32 CUDA tensor of shape [batch, N]")
         llr = llr.contiguous()
         w = weights.detach().contiguous().to(torch.float32)
+        if w.numel() != int(T) * code.base.shape[0]:
+            raise ValueError(f"weights must hold T x mb = {int(T) * code.base.shape[0]} values")
         B = llr.shape[0]
         need = C.c_size_t()
         _check("cbp_grad_workspace_bytes",
@@ -355,6 +359,10 @@ class _WeightedCBP(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, grad_soft):
+        if ctx.ws is None:
+            raise RuntimeError("weighted_cbp: backward ran a second time; the checkpoints of the "
+                               "forward pass are consumed by the first backward (run the "
+                               "forward again instead of retain_graph=True)")
         llr, w = ctx.saved_tensors
         gs = grad_soft.contiguous().to(torch.float32)
         gw = torch.empty_like(w)

@@ -181,6 +181,76 @@ def test_nms_single_check_by_hand():
         assert r["iters"][0] == 1 and r["hard"][0].tolist() == [1, 1, 0]
 
 
+def test_nms_two_checks_two_sweeps_by_hand():
+    """Layered normalized min-sum (Sec. II-B, Eqs. s2e10/s2e12 with the alpha of the min-sum
+    literature) worked by hand on two checks sharing two variables, alpha = 0.75, two sweeps.
+    Every value is a short binary fraction, so the FP32 and FP64 oracles must give exactly
+    these numbers.  CBP min-sum (Eqs. s4e18xx/s4e21xx, reading of the garbled text: unscaled
+    minima, first of equal minima wins) sends the same messages later, so it must too.
+
+    Checks: c0 = (v0, v1, v2), c1 = (v1, v2, v3); L = (2, -1, 3, 0.5).
+    Sweep 1, c0: Q = L = (2, -1, 3); min1 = 1 (v1), min2 = 2, one negative sign.
+        R = (-0.75*1, +0.75*2, -0.75*1) = (-0.75, 1.5, -0.75); Lambda = (1.25, 0.5, 2.25, 0.5)
+      c1: Q = (0.5, 2.25, 0.5); min1 = 0.5 (v1, first of the tie), min2 = 0.5 (v3), all +.
+        R = (0.375, 0.375, 0.375); Lambda = (1.25, 0.875, 2.625, 0.875)
+    Sweep 2, c0: Q = Lambda - R_old = (2, -0.625, 3.375); min1 = 0.625 (v1), min2 = 2.
+        R = (-0.46875, 1.5, -0.46875); Lambda = (1.53125, 0.875, 2.90625, 0.875)
+      c1: Q = (0.5, 2.53125, 0.5); min1 = min2 = 0.5.  R = (0.375, 0.375, 0.375)
+        Lambda = (1.53125, 0.875, 2.90625, 0.875)
+    A mistake in where alpha is applied (to the stored minima, to the rebuilt old message
+    only, or twice) changes these numbers."""
+    oc = O.OracleCode(np.array([[0, 0, 0, -1], [-1, 0, 0, 0]], np.int32), 1)
+    L = np.array([[2.0, -1.0, 3.0, 0.5]])
+    want = {1: [1.25, 0.875, 2.625, 0.875], 2: [1.53125, 0.875, 2.90625, 0.875]}
+    for alg in ("lbp_nms", "cbp_nms"):
+        for prec in (32, 64):
+            for sweeps, ref in want.items():
+                r = oc.decode(L, alg=alg, max_iter=sweeps, stop="none", alpha=0.75,
+                              precision=prec)
+                assert r["soft"][0].tolist() == ref, (alg, prec, sweeps)
+
+
+def layered_nms_by_exclusion(H_rows, L, alpha, sweeps):
+    """Textbook layered normalized min-sum in FP64, written from the definition with
+    explicit exclusion: the message of check m to its k-th variable is
+    alpha * prod_{j != k} sgn(q_j) * min_{j != k} |q_j| (no min1/min2/argmin bookkeeping);
+    checks in ascending order, Lambda updated after each check (Eqs. s2e10, s2e12)."""
+    lam = L.astype(np.float64).copy()
+    R = [np.zeros(len(r)) for r in H_rows]
+    for _ in range(sweeps):
+        for m, vs in enumerate(H_rows):
+            q = lam[vs] - R[m]
+            neg = q < 0.0
+            for k in range(len(vs)):
+                others = [j for j in range(len(vs)) if j != k]
+                mag = min(abs(q[j]) for j in others)
+                sign = np.logical_xor.reduce(neg[others])
+                R[m][k] = -(alpha * mag) if sign else alpha * mag
+            lam[vs] = q + R[m]
+    return lam
+
+
+@pytest.mark.parametrize("alpha", [0.75, 0.625, 1.0])
+def test_nms_equals_the_exclusion_definition(alpha):
+    """Both min-sum oracles (FP64) against layered NMS by explicit exclusion, bit for bit,
+    on the Z = 4 lift of the 576-bit base matrix over several sweeps."""
+    base = I.code_576().base
+    lift = np.where(base >= 0, base % 4, -1).astype(np.int32)
+    code = I.QCCode(lift, 4)
+    H = code.dense_H()
+    rows = [np.flatnonzero(H[m]) for m in range(H.shape[0])]
+    oc = O.OracleCode(lift, 4)
+    rng = np.random.default_rng(31)
+    for trial in range(4):
+        L = rng.normal(1.2, 2.0, size=code.N)
+        for sweeps in (1, 3, 6):
+            ref = layered_nms_by_exclusion(rows, L, alpha, sweeps)
+            for alg in ("lbp_nms", "cbp_nms"):
+                r = oc.decode(L[None], alg=alg, max_iter=sweeps, stop="none", alpha=alpha,
+                              precision=64)
+                assert np.array_equal(r["soft"][0], ref), (alg, trial, sweeps)
+
+
 # --------------------------------------------------------------------------- fixed points, symmetry
 @pytest.mark.parametrize("alg", ALGS32)
 def test_noiseless_codeword_decodes_in_one_sweep(c576, alg):

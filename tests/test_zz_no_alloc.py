@@ -64,3 +64,30 @@ def test_noalloc_rejects_a_code_too_big_for_the_scratch():
     assert rc == -5 and cbp.lib().cbp_strerror(rc) == b"workspace too small"
     torch.cuda.synchronize()
     assert iters.item() == 7   # nothing was launched
+
+
+def test_noalloc_fewer_lane_groups_per_cta_than_cbp_decode():
+    # Z = 256, 1000 base rows of degree 3 (two heavy columns, then one weight-1 column
+    # per row): one frame slot needs about 6 MB of scratch, and cbp_decode runs 3 lane
+    # groups per CTA, 18 MB together.  The no-alloc call drops to 2 groups per CTA (and a
+    # single CTA) to fit its array, and must still decode exactly like cbp_decode.
+    mb, Z = 1000, 256
+    rng = np.random.default_rng(11)
+    base = np.full((mb, 2 + mb), -1, dtype=np.int32)
+    base[:, 0] = rng.integers(0, Z, size=mb)
+    base[:, 1] = rng.integers(0, Z, size=mb)
+    base[np.arange(mb), 2 + np.arange(mb)] = 0
+    code = cbp.Code(base, Z)
+    frames = 320
+    li = code.launch_info(frames)
+    # cbp_decode: 3 lane groups of one frame each per CTA, check beliefs in the workspace
+    assert li["lane_groups_per_cta"] == 3 and li["frames_per_lane_group"] == 1
+    assert li["check_state_shared"] == 0 and li["frame_parallel"] == 0
+    g = torch.Generator(device="cuda").manual_seed(12)
+    for call in range(2):
+        x = 1.5 + 2.0 * torch.randn((frames, code.N), generator=g, device="cuda")
+        h_ref, i_ref = _reference(code, x, 3)
+        h, i = _noalloc(code, x, 3)
+        torch.cuda.synchronize()
+        assert torch.equal(i, i_ref), f"call {call}: iteration counts differ"
+        assert torch.equal(h, h_ref), f"call {call}: hard decisions differ"
