@@ -311,6 +311,11 @@ int cbp_decode_multi(const cbp_multi_item_t* items, int n_items, int max_iter,
  * on n device values: y[i] = phi(x[i]).  x, y device, 4-byte aligned, n >= 0. */
 int cbp_phi(const float* x, float* y, int64_t n, cbp_stream_t stream);
 
+/* The derivative of that phi as the library evaluates it (the adjoint cbp_decode_grad
+ * uses for Eq. s2e5): the derivative of the cubic of x's grid centre, 0 where the clamp
+ * holds (x below fl32(phi(30)) or above 30).  Same arguments as cbp_phi. */
+int cbp_phi_deriv(const float* x, float* y, int64_t n, cbp_stream_t stream);
+
 /* Device status of a code handle.  Kernels never trap on bad input: they set a bit in
  * the handle's status word and carry on (the frame's results are then undefined).
  *   CBP_STATUS_NONFINITE_LLR  some decoded frame's channel LLRs held NaN or +-Inf

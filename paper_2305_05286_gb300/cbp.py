@@ -28,6 +28,7 @@ EXPORTS = ("cbp_code_create", "cbp_code_destroy", "cbp_code_info", "cbp_workspac
            "cbp_decode_host", "cbp_grad_workspace_bytes",
            "cbp_decode_weighted", "cbp_decode_grad", "cbp_decode_noalloc",
            "cbp_multi_workspace_bytes", "cbp_multi_launch_info", "cbp_decode_multi", "cbp_phi",
+           "cbp_phi_deriv",
            "cbp_edge_ceiling", "cbp_device_status", "cbp_strerror")
 STATUS_NONFINITE_LLR = 1
 MULTI_MAX_ITEMS = 8
@@ -103,6 +104,8 @@ def lib(build_if_needed: bool = True):
             L.cbp_decode_multi.argtypes = [MI, I, I, P, Z, P, MO]
             L.cbp_phi.restype = I
             L.cbp_phi.argtypes = [P, P, C.c_int64, P]
+            L.cbp_phi_deriv.restype = I
+            L.cbp_phi_deriv.argtypes = [P, P, C.c_int64, P]
             L.cbp_device_status.restype = I
             L.cbp_device_status.argtypes = [P, P, C.POINTER(C.c_uint32)]
             L.cbp_edge_ceiling.restype = I
@@ -297,6 +300,18 @@ def phi(x: torch.Tensor, stream=None) -> torch.Tensor:
     x = x.contiguous()
     y = torch.empty_like(x)
     _check("cbp_phi", lib().cbp_phi(x.data_ptr(), y.data_ptr(), x.numel(), _stream_ptr(stream)))
+    return y
+
+
+def phi_deriv(x: torch.Tensor, stream=None) -> torch.Tensor:
+    """Derivative of the library's FP32 phi as evaluated (cbp_phi_deriv): the derivative of
+    the cubic of each input's grid centre, 0 where the clamp holds."""
+    if x.dtype != torch.float32 or not x.is_cuda:
+        raise ValueError("x must be a float32 CUDA tensor")
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    _check("cbp_phi_deriv",
+           lib().cbp_phi_deriv(x.data_ptr(), y.data_ptr(), x.numel(), _stream_ptr(stream)))
     return y
 
 

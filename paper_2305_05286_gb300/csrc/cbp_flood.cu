@@ -173,12 +173,13 @@ __global__ void __launch_bounds__(768, 1) flood_kernel(const KParams p) {
   }
 }
 
+template <bool DERIV>
 __global__ void phi_kernel(const float* __restrict__ x, float* __restrict__ y, long long n,
                            const float4* __restrict__ tab, float xlo) {
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
   for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += stride)
-    y[i] = phi_eval(x[i], xlo, tab);
+    y[i] = DERIV ? phi_deriv(x[i], xlo, tab) : phi_eval(x[i], xlo, tab);
 }
 
 }  // namespace
@@ -197,11 +198,14 @@ cudaError_t launch_status_take(uint32_t* status, cudaStream_t st) {
 }
 
 cudaError_t launch_phi(const float* x, float* y, long long n, const float4* tab, float xlo,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool deriv) {
   if (n <= 0) return cudaSuccess;
   long long blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
-  phi_kernel<<<static_cast<int>(blocks), 256, 0, st>>>(x, y, n, tab, xlo);
+  if (deriv)
+    phi_kernel<true><<<static_cast<int>(blocks), 256, 0, st>>>(x, y, n, tab, xlo);
+  else
+    phi_kernel<false><<<static_cast<int>(blocks), 256, 0, st>>>(x, y, n, tab, xlo);
   return cudaGetLastError();
 }
 

@@ -222,6 +222,7 @@ using namespace cbp;
 struct cbp_code {
   int dev = 0;
   int mb = 0, nb = 0, Z = 0, N = 0, M = 0, E = 0, K = -1, nnzb = 0, maxdeg = 0;
+  int test_row = 0;          // a base row of the largest degree (the sweep-end pre-test)
   int ncomp = 0, nself = 0;  // columns of weight >= 2 / of weight 1
   bool self_last = true;     // every row holds at most one weight-1 entry, as its last
   CodeDev d;
@@ -485,6 +486,7 @@ KParams code_params(const cbp_code* c, const DeviceInfo& di, const Plan& pl, int
   p.team_groups = team_groups_for(c->Z, pl.F);
   p.slots = pl.grid * pl.F * pl.v.fpt;
   p.maxdeg = c->maxdeg;
+  p.test_row = c->test_row;
   p.ncomp = c->ncomp;
   p.nself = c->nself;
   p.ws_slot = pl.ws.slot;
@@ -606,6 +608,11 @@ int cbp_code_create(const int32_t* base, int mb, int nb, int Z, cbp_code_t** out
   c->nnzb = nnzb;
   c->E = nnzb * Z;
   c->maxdeg = maxdeg;
+  for (int r = 0; r < mb; ++r)
+    if (rptr[r + 1] - rptr[r] == maxdeg) {
+      c->test_row = r;
+      break;
+    }
   c->ncomp = ncomp;
   c->nself = nself;
   // K = N - rank(H): full rank when the parity part is block lower-triangular with
@@ -1296,16 +1303,26 @@ int cbp_decode_multi(const cbp_multi_item_t* items, int n_items, int max_iter, v
              : CBP_ECUDA;
 }
 
-int cbp_phi(const float* x, float* y, int64_t n, cbp_stream_t stream) {
+namespace {
+int phi_call(const float* x, float* y, int64_t n, cbp_stream_t stream, bool deriv) {
   if (n < 0) return CBP_EINVAL;
   if (n == 0) return CBP_OK;
   if (!x || !y || !aligned(x, 4) || !aligned(y, 4)) return CBP_EINVAL;
   DeviceInfo* di = nullptr;
   if (int rc = current_device(&di, nullptr)) return rc;
-  return launch_phi(x, y, n, di->tab, di->xlo, reinterpret_cast<cudaStream_t>(stream)) ==
-                 cudaSuccess
+  return launch_phi(x, y, n, di->tab, di->xlo, reinterpret_cast<cudaStream_t>(stream),
+                    deriv) == cudaSuccess
              ? CBP_OK
              : CBP_ECUDA;
+}
+}  // namespace
+
+int cbp_phi(const float* x, float* y, int64_t n, cbp_stream_t stream) {
+  return phi_call(x, y, n, stream, false);
+}
+
+int cbp_phi_deriv(const float* x, float* y, int64_t n, cbp_stream_t stream) {
+  return phi_call(x, y, n, stream, true);
 }
 
 int cbp_device_status(const cbp_code_t* c, cbp_stream_t stream, uint32_t* flags) {

@@ -143,6 +143,7 @@ struct KParams {
   int team_groups;       // lane groups per independently synchronised team (>= F: one team)
   int slots;             // frame slots of the launch: gridDim.x * F * fpt
   int maxdeg;
+  int test_row;          // CBP-SP: base row whose checks are tested first at a sweep's end
   int ncomp, nself;      // columns of weight >= 2 / of weight 1
   long long ws_slot;     // floats of workspace per lane group
   long long ws_cta;      // CBP-SP: floats of workspace per CTA (>= F * ws_slot)
@@ -213,7 +214,7 @@ void* fp_kernel_ptr();                                       // cbp_fp.cu
 int fp_threads();                                            // cbp_fp.cu: threads per CTA
 void* flood_kernel_ptr();              // cbp_flood.cu
 cudaError_t launch_phi(const float* x, float* y, long long n, const float4* tab, float xlo,
-                       cudaStream_t st);
+                       cudaStream_t st, bool deriv);
 cudaError_t launch_status_take(uint32_t* status, cudaStream_t st);  // cbp_flood.cu
 // CBP-SP edge-update ceiling (cbp_ceiling.cu): 512 threads per CTA.
 cudaError_t launch_edge_ceiling(const float4* tab, float xlo, int blocks, int iters,

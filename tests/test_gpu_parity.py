@@ -151,6 +151,33 @@ def test_full_size_26112_sampled(large):
     assert ((np.abs(iters.cpu().numpy()) >= 1) & (np.abs(iters.cpu().numpy()) <= 20)).all()
 
 
+def test_full_size_26112_at_the_operating_point(large):
+    """The benchmark's launch (65536 frames of the 26112-bit code at 2.5 dB, the bench's
+    own frames) against the oracle on 4 frames of every frame slot: the slot's first frame,
+    its second (the first reload), one from the middle of its run and its last, so every
+    slot and several reload rounds are compared bit for bit (hard decisions, iteration
+    counts, soft outputs)."""
+    qc, code, oc = large
+    B = 65536
+    info = code.launch_info(B)
+    slots = info["ctas"] * info["lane_groups_per_cta"] * info["frames_per_lane_group"]
+    assert info["frame_parallel"] == 0 and slots >= 152
+    llr, cw = I.make_frames_torch(qc, B, 2.5, seed=2000)
+    hard, iters, soft = code.decode(llr, max_iter=20, alg="cbp_sp", soft=True)
+    torch.cuda.synchronize()
+    k = np.arange(slots)
+    last = k + ((B - 1 - k) // slots) * slots
+    pick = np.unique(np.concatenate([k, k + slots, k + 100 * slots, last]))
+    assert pick.size >= 1024 and pick.max() < B
+    idx = torch.from_numpy(pick).cuda()
+    ref = oc.decode(llr[idx].cpu().numpy(), alg="cbp_sp", max_iter=20, threads=THREADS)
+    got = (cbp.unpack_bits(hard[idx], qc.N).cpu().numpy(), iters[idx].cpu().numpy(),
+           soft[idx].cpu().numpy())
+    assert_parity(got, ref, "26112 at 2.5 dB, every slot")
+    it = iters.cpu().numpy()
+    assert (it != 0).all() and np.abs(it).max() <= 20 and np.abs(it).mean() > 3
+
+
 @pytest.mark.parametrize("alg", ALGS)
 def test_sign_symmetry_on_gpu(code576, alg):
     qc, code, oc = code576
