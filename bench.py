@@ -439,34 +439,57 @@ def run_ours(args, rank, world, dist):
 
 
 def run_sweep(args):
+    """FER, BER, mean sweeps and decoded Gbit/s per Eb/N0 point for each decoder, on the
+    26112-bit code (65536 device frames per point by default, at most 20 sweeps) or on the
+    576-bit code (2000 GF(2)-encoded frames per point, at most 30 sweeps).  Every point is
+    timed over --sweep-steps launches after one warm-up, with its own clock record and ALU
+    roofline fraction; one JSON line per (point, decoder)."""
     import torch
 
     from paper_2305_05286_gb300 import cbp
     from paper_2305_05286_gb300 import inputs as I
 
-    qc = I.code_26112()
+    qc = bench_code(I, args.code)
     K = (qc.nb - qc.mb) * qc.Z
     code = cbp.Code.from_qc(qc)
-    B = args.sweep_frames
+    small = qc.N <= 4096
+    B = args.sweep_frames if args.sweep_frames else (2000 if small else FRAMES)
+    max_iter = args.sweep_max_iter if args.sweep_max_iter else (30 if small else MAX_ITER)
     stream = torch.cuda.current_stream()
-    rows = []
-    for i, e in enumerate(np.arange(args.sweep_lo, args.sweep_hi + 1e-9, 0.25)):
-        llr, cw = I.make_frames_torch(qc, B, float(e), seed=2000 + i)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    gid = gpu_identity(torch, 0)
+    points = np.arange(args.sweep_lo, args.sweep_hi + 1e-9, args.sweep_step)
+    for i, e in enumerate(points):
+        if small:  # the parity workload's host frames (GF(2) encoder)
+            fr = I.make_frames(qc, B, float(e), seed=1000 + int(round(float(e) * 10)))
+            llr = torch.from_numpy(fr.llr).cuda()
+            cw = torch.from_numpy(fr.codewords).cuda()
+        else:
+            llr, cw = I.make_frames_torch(qc, B, float(e), seed=2000 + i,
+                                          zero_codeword=not I.is_lower_triangular(qc))
         hard = torch.empty((B, code.words), dtype=torch.int32, device="cuda")
         iters = torch.empty((B,), dtype=torch.int32, device="cuda")
         for alg in args.sweep_algs.split(","):
             ws = code.workspace(B, alg)
-            f = lambda: code.decode_into(llr, hard, iters, max_iter=MAX_ITER, alg=alg,
+            f = lambda: code.decode_into(llr, hard, iters, max_iter=max_iter, alg=alg,
                                          alpha=args.alpha, workspace=ws)
             f()
             torch.cuda.synchronize()
-            ms = timed_steps(torch, f, 1, stream)
-            s = frame_stats(torch, cbp, qc, hard, iters, cw)
-            row = {"ebn0_db": float(e), "alg": alg, "frames": B, "fer": s["fer"], "ber": s["ber"],
-                   "alpha": args.alpha if "nms" in alg else None,
-                   "mean_iters": s["mean_iters"], "gbps": K * B / (ms / 1e3) / 1e9, "ms": ms}
-            rows.append(row)
+            with ClockSampler(gid) as clk:
+                ms = timed_steps(torch, f, args.sweep_steps, stream)
+                torch.cuda.synchronize()
+            st = frame_stats(torch, cbp, qc, hard, iters, cw)
+            clocks = clk.summary()
+            peak = sms * 128 * (clocks["sm_mhz"] or 2070.0) * 1e6 / 1e12
+            ro = roofline_entry(alg, qc, st, ms, peak, args.code, None)
+            row = {"code": f"{qc.mb}x{qc.nb} Z={qc.Z} (N={qc.N}, K={K})", "ebn0_db": round(float(e), 3),
+                   "alg": alg, "alpha": args.alpha if "nms" in alg else None, "frames": B,
+                   "max_iter": max_iter, "fer": st["fer"], "ber": st["ber"],
+                   "mean_iters": st["mean_iters"], "gbps": K * B / (ms / 1e3) / 1e9,
+                   "ms_per_launch": ms, "launches": args.sweep_steps,
+                   "alu_frac": ro["frac"], "clocks": clocks}
             print(json.dumps(row), flush=True)
+            del ws
         del llr, cw
 
 
@@ -736,7 +759,13 @@ def main():
     ap.add_argument("--ebn0", type=float, default=EBN0_OPERATING)
     ap.add_argument("--frames", type=int, default=FRAMES)
     ap.add_argument("--sweep", action="store_true")
-    ap.add_argument("--sweep-frames", type=int, default=16384)
+    ap.add_argument("--sweep-frames", type=int, default=0,
+                    help="frames per Eb/N0 point (0: 65536 for the 26112-bit code, 2000 for "
+                         "the 576-bit code)")
+    ap.add_argument("--sweep-step", type=float, default=0.25)
+    ap.add_argument("--sweep-steps", type=int, default=3, help="timed launches per point")
+    ap.add_argument("--sweep-max-iter", type=int, default=0,
+                    help="0: 20 sweeps for the 26112-bit code, 30 for the 576-bit code")
     ap.add_argument("--sweep-algs", default="cbp_sp,cbp_nms,lbp_nms,fbp_sp")
     ap.add_argument("--alpha", type=float, default=0.75,
                     help="min-sum normalisation for --sweep (the bench line uses 0.75)")

@@ -329,6 +329,48 @@ __device__ __forceinline__ void sweep_rows(int mb, bool any, const int* s_rptr,
   }
 }
 
+// Sweep-end pre-test: lane z evaluates the flushed posterior (Eq. s4e20, read-only) of
+// each variable of check (test row, z) and folds its hard decision (Eq. s2e7) into
+// par[h]; an odd par[h] is an unsatisfied check, so frame h's syndrome is non-zero.
+// The variable of entry (r, c, s) is position a = (z + s) mod Z of column c; its last
+// check is (rk, (a - sk) mod Z) for the last entry (rk, c, sk) of the column (for a
+// weight-1 column: (r, z) itself, its state kept by lane z).
+template <int FPT>
+__device__ __forceinline__ void test_row_parity(const KParams& p, const int* s_rptr,
+                                                const uint2* s_col, int z, int Z, float xlo,
+                                                const float4* __restrict__ tab, const float* QP,
+                                                const float* SV, const float* S, uint32_t* par) {
+  using LV = Lanes<FPT>;
+  const int k0 = s_rptr[p.test_row], k1 = s_rptr[p.test_row + 1];
+#pragma unroll 1
+  for (int k = k0; k < k1; ++k) {
+    const BaseEdge be = p.edges[k];  // read through L1, like the syndrome scan
+    const uint2 ci = s_col[be.c];
+    const int idx = ci.y & 0xffff;
+    const int sk = int(ci.x >> 16), rk = int(ci.x & 0xffff);
+    float qv[FPT], pv[FPT], Sk[FPT];
+    if (ci.y & 0x10000u) {
+      LV::ld_pair(SV, idx * Z + z, qv, pv);
+      LV::ld(S, rk * Z + z, Sk);
+    } else {
+      const int a = mod_add(z + be.s, Z);
+      LV::ld_pair(QP, idx * Z + a, qv, pv);
+      int zk = a - sk;
+      zk = zk < 0 ? zk + Z : zk;
+      LV::ld(S, rk * Z + zk, Sk);
+    }
+#pragma unroll
+    for (int h = 0; h < FPT; ++h) {
+      const float mag = phi_eval(fabsf(__fsub_rn(fabsf(Sk[h]), pv[h])), xlo, tab);
+      const float lb = __fadd_rn(
+          qv[h], __uint_as_float(__float_as_uint(mag) |
+                                 ((__float_as_uint(Sk[h]) ^ __float_as_uint(qv[h])) &
+                                  0x80000000u)));
+      par[h] ^= lb < 0.0f ? 1u : 0u;
+    }
+  }
+}
+
 // Decode frames frame0, frame0 + 1, ... of one code with the lane groups of this CTA:
 // frame slot k starts at frame0 + k and advances by `stride` when its frame stops, until
 // it passes `end`.  Returns when every slot of the CTA is idle.
@@ -393,8 +435,8 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
   // lane (4 ints) and one ok byte per check lane
   int* wst = reinterpret_cast<int*>(bits + FPT * wpad);
   unsigned char* okb = reinterpret_cast<unsigned char*>(wst + 4);
-  if (WIN && lane)
-    for (int w = z; w < wpad; w += Z) bits[w] = 0u;
+  if (lane)  // WIN: [latest posterior < 0]; otherwise the decision bits of a full test
+    for (int w = z; w < FPT * wpad; w += Z) bits[w] = 0u;
   SlotState* my = s_slot + (lane ? g : 0) * FPT;
   const float4* tab = s_tab;
   const float xlo = p.phi_xlo;
@@ -445,7 +487,9 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
     sweep_rows<FPT, CH, DB, WIN, SELFLAST>(p.mb, any, s_rptr, s_spe, z, Z, later, t, xlo, tab,
                                            QP, SV, S, R, bar_id, bar_n, p.edges, bits, wst,
                                            okb, M, halted);
-    bool done[FPT];
+    bool done[FPT], full[FPT];
+#pragma unroll
+    for (int h = 0; h < FPT; ++h) full[h] = false;
     if constexpr (WIN) {
       // Step 3: the hard decisions of the latest V2C phase; iters = the sweep in which
       // the window filled, negated when it never did
@@ -459,75 +503,107 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
       if (done[0])
         for (int w = z; w < wpad; w += Z) bits[w] = 0u;  // ready for the slot's next frame
     } else {
-      // ---- flushed posterior, hard decisions (Eq. s2e7)
-  #pragma unroll
-      for (int h = 0; h < FPT; ++h)
-        if (act[h])
-          for (int w = z; w < words; w += Z) bits[h * wpad + w] = 0u;
+      // ---- end of the sweep: flushed posterior (Eq. s4e20 read-only), hard decisions
+      // (Eq. s2e7) and the syndrome stop.  A frame stops only when every check holds, so
+      // the checks of one base row (the test row) are evaluated first; when one of them
+      // fails, the frame goes on and the full flush and syndrome scan are skipped (the
+      // syndrome is non-zero whatever the other rows give: the same decision).
       if (lane && z == 0)
   #pragma unroll
         for (int h = 0; h < FPT; ++h) my[h].unsat = 0;
       team_sync(bar_id, bar_n);
-      for (int c = 0; c < p.nb; ++c) {
-        const uint2 ci = s_col[c];
-        const int idx = ci.y & 0xffff;
-        const int sk = int(ci.x >> 16), rk = int(ci.x & 0xffff);
-        float qv[FPT], pv[FPT], Sk[FPT];
-        int v = 0;
-        if (any) {
-          if (ci.y & 0x10000u) {  // weight-1 column: lane z owns its single check (rk, z)
-            LV::ld_pair(SV, idx * Z + z, qv, pv);
-            LV::ld(S, rk * Z + z, Sk);
-            v = c * Z + mod_add(z + sk, Z);
-          } else {
-            LV::ld_pair(QP, idx * Z + z, qv, pv);
-            int zk = z - sk;
-            zk = zk < 0 ? zk + Z : zk;
-            LV::ld(S, rk * Z + zk, Sk);
-            v = c * Z + z;
-          }
-        }
+      if (p.stop == CBP_STOP_SYNDROME && any) {
+        bool test[FPT];
+        bool tany = false;
   #pragma unroll
         for (int h = 0; h < FPT; ++h) {
-          bool neg = false;
-          if (act[h]) {
-            const float mag = phi_eval(fabsf(__fsub_rn(fabsf(Sk[h]), pv[h])), xlo, tab);
-            const float lb = __fadd_rn(
-                qv[h], __uint_as_float(__float_as_uint(mag) |
-                                       ((__float_as_uint(Sk[h]) ^ __float_as_uint(qv[h])) &
-                                        0x80000000u)));
-            neg = lb < 0.0f;
-            if (p.soft) p.soft[static_cast<long long>(frame[h]) * N + v] = lb;
-          }
-          if (words_aligned) {
-            // Z % 32 == 0: a warp lies inside one lane group, and its 32 variables of
-            // column c are 32 consecutive positions of the column (rotated by the shift
-            // for a weight-1 column), i.e. one aligned word or two partial ones
-            const unsigned wv = __ballot_sync(0xffffffffu, neg);
-            if ((tid & 31) == 0 && act[h]) {
-              uint32_t* wb = bits + h * wpad;
-              const int p0 = v - c * Z;  // position of this lane's variable in column c
-              const int sh = p0 & 31;
-              if (sh == 0) {
-                wb[v >> 5] = wv;  // the word holds exactly this warp's variables
-              } else {
-                atomicOr(wb + (v >> 5), wv << sh);
-                atomicOr(wb + ((c * Z + mod_add(p0 - sh + 32, Z)) >> 5), wv >> (32 - sh));
-              }
+          test[h] = act[h] && t[h] < p.max_iter;
+          tany |= test[h];
+        }
+        if (tany) {
+          uint32_t par[FPT];
+  #pragma unroll
+          for (int h = 0; h < FPT; ++h) par[h] = 0;
+          test_row_parity<FPT>(p, s_rptr, s_col, z, Z, xlo, tab, QP, SV, S, par);
+  #pragma unroll
+          for (int h = 0; h < FPT; ++h)
+            if (test[h] && par[h]) my[h].unsat = 1;
+        }
+      }
+      team_sync(bar_id, bar_n);
+      bool any_full = false;
+  #pragma unroll
+      for (int h = 0; h < FPT; ++h) {
+        full[h] = act[h] && (t[h] >= p.max_iter ||
+                             (p.stop == CBP_STOP_SYNDROME &&
+                              *static_cast<volatile int*>(&my[h].unsat) == 0));
+        any_full |= full[h];
+      }
+      // the decision bits of every frame are zero here (cleared at the start and after
+      // each full test); the warp skips the flush when none of its frames needs it
+      if (__any_sync(0xffffffffu, any_full)) {
+        for (int c = 0; c < p.nb; ++c) {
+          const uint2 ci = s_col[c];
+          const int idx = ci.y & 0xffff;
+          const int sk = int(ci.x >> 16), rk = int(ci.x & 0xffff);
+          float qv[FPT], pv[FPT], Sk[FPT];
+          int v = 0;
+          if (any_full) {
+            if (ci.y & 0x10000u) {  // weight-1 column: lane z owns its single check (rk, z)
+              LV::ld_pair(SV, idx * Z + z, qv, pv);
+              LV::ld(S, rk * Z + z, Sk);
+              v = c * Z + mod_add(z + sk, Z);
+            } else {
+              LV::ld_pair(QP, idx * Z + z, qv, pv);
+              int zk = z - sk;
+              zk = zk < 0 ? zk + Z : zk;
+              LV::ld(S, rk * Z + zk, Sk);
+              v = c * Z + z;
             }
-          } else {
-            warp_or_bit(bits + h * wpad + (v >> 5), neg ? (1u << (v & 31)) : 0u, act[h]);
+          }
+  #pragma unroll
+          for (int h = 0; h < FPT; ++h) {
+            bool neg = false;
+            if (full[h]) {
+              const float mag = phi_eval(fabsf(__fsub_rn(fabsf(Sk[h]), pv[h])), xlo, tab);
+              const float lb = __fadd_rn(
+                  qv[h], __uint_as_float(__float_as_uint(mag) |
+                                         ((__float_as_uint(Sk[h]) ^ __float_as_uint(qv[h])) &
+                                          0x80000000u)));
+              neg = lb < 0.0f;
+              if (p.soft) p.soft[static_cast<long long>(frame[h]) * N + v] = lb;
+            }
+            if (words_aligned) {
+              // Z % 32 == 0: a warp lies inside one lane group, and its 32 variables of
+              // column c are 32 consecutive positions of the column (rotated by the shift
+              // for a weight-1 column), i.e. one aligned word or two partial ones
+              const unsigned wv = __ballot_sync(0xffffffffu, neg);
+              if ((tid & 31) == 0 && full[h]) {
+                uint32_t* wb = bits + h * wpad;
+                const int p0 = v - c * Z;  // position of this lane's variable in column c
+                const int sh = p0 & 31;
+                if (sh == 0) {
+                  wb[v >> 5] = wv;  // the word holds exactly this warp's variables
+                } else {
+                  atomicOr(wb + (v >> 5), wv << sh);
+                  atomicOr(wb + ((c * Z + mod_add(p0 - sh + 32, Z)) >> 5), wv >> (32 - sh));
+                }
+              }
+            } else {
+              warp_or_bit(bits + h * wpad + (v >> 5), neg ? (1u << (v & 31)) : 0u, full[h]);
+            }
           }
         }
       }
       team_sync(bar_id, bar_n);
-      // ---- syndrome; a frame stops scanning once one of its checks is unsatisfied
-      if (any) {
+      // ---- syndrome of the frames tested in full; a frame stops scanning once one of
+      // its checks is unsatisfied
+      if (any_full) {
         bool open[FPT];
         bool scan = false;
   #pragma unroll
         for (int h = 0; h < FPT; ++h) {
-          open[h] = act[h];
+          open[h] = full[h];
           scan |= open[h];
         }
         for (int r = 0; r < p.mb && scan; ++r) {
@@ -553,7 +629,7 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
   #pragma unroll
       for (int h = 0; h < FPT; ++h) {
         done[h] = false;
-        if (act[h]) {
+        if (full[h]) {
           const bool ok = my[h].unsat == 0;
           done[h] = (ok && p.stop == CBP_STOP_SYNDROME) || t[h] >= p.max_iter;
           if (done[h]) {
@@ -565,6 +641,12 @@ __device__ __forceinline__ void sp_body(const KParams& p, int frame0, int stride
       }
     }  // not WIN
     team_sync(bar_id, bar_n);
+    if constexpr (!WIN) {
+  #pragma unroll
+      for (int h = 0; h < FPT; ++h)  // ready for the next full test
+        if (full[h])
+          for (int w = z; w < words; w += Z) bits[h * wpad + w] = 0u;
+    }
     if (z == 0) {
 #pragma unroll
       for (int h = 0; h < FPT; ++h)
