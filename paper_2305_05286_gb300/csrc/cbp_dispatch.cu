@@ -10,7 +10,7 @@ static void* select_kernel(const Variant& v) {
       return v.win ? sp_win_kernel_ptr(v.chk_shared)
                    : sp_kernel_ptr(v.chk_shared, v.fpt, v.wide, v.self_last);
     case ALG_CBP_NMS:
-    case ALG_LBP_NMS: return minsum_kernel_ptr(v.alg, v.chk_shared);
+    case ALG_LBP_NMS: return minsum_kernel_ptr(v.alg, v.chk_shared, v.rstore);
     case ALG_FBP_SP: return flood_kernel_ptr();
   }
   return nullptr;

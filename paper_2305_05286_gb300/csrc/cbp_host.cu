@@ -113,6 +113,8 @@ int device_init(int dev, DeviceInfo** out) {
                            {ALG_CBP_SP, false, 1, false, false, true},
                            {ALG_CBP_SP, false, 1, false, false, false, true},
                            {ALG_CBP_NMS, true, 1}, {ALG_CBP_NMS, false, 1},
+                           {ALG_CBP_NMS, true, 1, false, false, false, false, true},
+                           {ALG_CBP_NMS, false, 1, false, false, false, false, true},
                            {ALG_LBP_NMS, false, 1}, {ALG_FBP_SP, false, 1}};
     for (const Variant& v : all)
       if (decoder_set_smem(v, d.smem_optin) != cudaSuccess) return CBP_ECUDA;
@@ -198,11 +200,12 @@ WsLayout ws_layout(const Variant& v, const Shape& s) {
       }
       break;
     case ALG_CBP_NMS:
-    case ALG_LBP_NMS:  // weight-1 column state | per-check state (uint4) | CBP (min1, min2)
+    case ALG_LBP_NMS:  // weight-1 column state | per-check state (uint4; with per-edge
+                       // messages: R [E]) | CBP (min1, min2)
       w.off_sv = 0;
       f = align64(static_cast<size_t>(s.nself) * s.Z);
       w.off_s = static_cast<long long>(f);
-      f += align64(4 * static_cast<size_t>(s.M));
+      f += v.rstore ? align64(static_cast<size_t>(s.E)) : align64(4 * static_cast<size_t>(s.M));
       if (v.alg == ALG_CBP_NMS && !v.chk_shared) {
         w.off_c = static_cast<long long>(f);
         f += align64(2 * static_cast<size_t>(s.M));
@@ -362,6 +365,8 @@ int make_lane_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, 
     case ALG_CBP_NMS:
       if (c->maxdeg > kMaxDegCbpMs) return CBP_EUNSUPPORTED;
       cands = {{ALG_CBP_NMS, true}, {ALG_CBP_NMS, false}};
+      if (const char* e = std::getenv("CBP_PLAN_NMS_R"); e && e[0] == '1')
+        for (Variant& v : cands) v.rstore = true;
       break;
     case ALG_LBP_NMS:
       if (c->maxdeg > kMaxDeg) return CBP_EUNSUPPORTED;

@@ -184,6 +184,7 @@ struct Variant {
   bool win = false;   // CBP-SP with the paper-literal stop (CBP_STOP_WINDOW)
   bool self_last = false;  // CBP-SP, one frame per group: every weight-1 edge ends its row
   bool fp = false;         // CBP-SP, frame-parallel kernel: one frame per thread
+  bool rstore = false;     // CBP min-sum: C2V messages kept per edge (no rebuild)
 };
 
 // Sizes that fix the shared-memory and workspace layout of a launch.
@@ -209,7 +210,7 @@ void* sp_multi_kernel_ptr(bool chk_shared, int fpt, bool self_last);  // cbp_sp.
 void* sp_win_kernel_ptr(bool chk_shared);                   // cbp_sp.cu
 cudaError_t launch_multi(bool chk_shared, int fpt, bool self_last, const MultiParams& mp, int grid,
                          int threads, size_t smem, cudaStream_t st);
-void* minsum_kernel_ptr(int alg, bool chk_shared);          // cbp_minsum.cu
+void* minsum_kernel_ptr(int alg, bool chk_shared, bool rstore);  // cbp_minsum.cu
 void* fp_kernel_ptr();                                       // cbp_fp.cu
 int fp_threads();                                            // cbp_fp.cu: threads per CTA
 void* flood_kernel_ptr();              // cbp_flood.cu

@@ -88,9 +88,14 @@ __device__ __forceinline__ void lbp_row(const BaseEdge* __restrict__ s_e, int k0
   AUX[m] = make_uint4(__float_as_uint(sig ? -m1 : m1), __float_as_uint(m2), idx, sg);
 }
 
-template <int ALG, bool CHKS, int MAXT>
+// RST (CBP min-sum only): the C2V messages are kept per edge in the workspace, R [base
+// entry][lane] as in the CBP log-tanh kernel: B2V stores R^new in the predecessor's slot
+// (Eq. s4e22) and V2C reads the edge's own slot, so the check state shrinks to
+// (min1 | sgn, min2) and no old message is rebuilt.
+template <int ALG, bool CHKS, int MAXT, bool RST = false>
 __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
   constexpr bool CBP = (ALG == ALG_CBP_NMS);
+  static_assert(!RST || CBP, "per-edge messages: CBP min-sum only");
   extern __shared__ __align__(16) unsigned char smem[];
   const int Z = p.Z, N = p.N, M = p.M, words = p.words, G = p.F;
   const int tid = threadIdx.x;
@@ -130,7 +135,8 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
   const long long gslot = static_cast<long long>(blockIdx.x) * G + (lane ? g : 0);
   float* wsl = p.ws + gslot * p.ws_slot;
   float* SV = wsl + p.ws_off_sv;                          // [nself*Z]
-  uint4* AUX = reinterpret_cast<uint4*>(wsl + p.ws_off_s);  // [M]
+  uint4* AUX = reinterpret_cast<uint4*>(wsl + p.ws_off_s);  // [M] (not RST)
+  float* Rg = wsl + p.ws_off_s;                           // [E] (RST)
   float2* CHK = nullptr;                                  // [M] (CBP)
   if (CBP) {
     if (CHKS) {
@@ -142,6 +148,8 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
   }
   uint32_t* bits = reinterpret_cast<uint32_t*>(nxt);
   SlotState* my = s_slot + (lane ? g : 0);
+  if (lane)
+    for (int w = z; w < ((words + 3) & ~3); w += Z) bits[w] = 0u;
   const int tg = p.team_groups;
   const bool single_team = tg >= G;
   const int bar_id = single_team ? 0 : 1 + (lane ? g / tg : 0);
@@ -177,7 +185,7 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
           float r1 = 0.0f, r2 = 0.0f;
           uint32_t osig = 0, oidx = 0;
           unsigned long long osg = 0;
-          if (t > 1) {
+          if (!RST && t > 1) {
             const float2 cs = CHK[m];
             const uint4 a = AUX[m];
             r1 = __fmul_rn(alpha, fabsf(cs.x));
@@ -190,9 +198,9 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
           uint32_t idx = 0, sig = 0;
           unsigned long long sg = 0;
           for (int j0 = 0; j0 < d; j0 += 4) {
-            float q[4];
+            float q[4], ro[4];
             float2 pc[4];
-            int qoff[4];
+            int qoff[4], roff[4];
             uint32_t fl[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -207,6 +215,10 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
                 int zj = zv - be.ps;
                 zj = zj < 0 ? zj + Z : zj;
                 pc[u] = CHK[be.pr * Z + zj];
+                if (RST) {  // own slot (c_i -> v), predecessor slot (c_j -> v)
+                  ro[u] = (t > 1 && !(be.flags & kSelf)) ? Rg[(k0 + j) * Z + z] : 0.0f;
+                  roff[u] = be.pe * Z + zj;
+                }
               }
             }
 #pragma unroll
@@ -223,6 +235,9 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
                 float rold = 0.0f;
                 if (fl[u] & kSelf) {
                   rold = Rn;                                   // c_j == c_i
+                } else if (RST) {
+                  rold = ro[u];
+                  if (!(t == 1 && (fl[u] & kFirst))) Rg[roff[u]] = Rn;  // Eq. (s4e22)
                 } else if (t > 1) {
                   const float rm = (static_cast<uint32_t>(j) == oidx) ? r2 : r1;
                   rold = (osig ^ static_cast<uint32_t>((osg >> j) & 1ull)) ? -rm : rm;
@@ -238,14 +253,15 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
                 }
                 const uint32_t neg = qn < 0.0f;
                 sig ^= neg;
-                sg |= static_cast<unsigned long long>(neg) << j;
+                if (!RST) sg |= static_cast<unsigned long long>(neg) << j;
                 if (fl[u] & kSelf) SV[qoff[u]] = qn;
                 else VAR[qoff[u]] = qn;
               }
             }
           }
           CHK[m] = make_float2(sig ? -m1 : m1, m2);
-          AUX[m] = make_uint4(idx, static_cast<uint32_t>(sg), static_cast<uint32_t>(sg >> 32), 0u);
+          if (!RST)
+            AUX[m] = make_uint4(idx, static_cast<uint32_t>(sg), static_cast<uint32_t>(sg >> 32), 0u);
         } else {
           // layered NMS, unrolled for the smallest degree bucket that holds the row
           if (d <= 8) lbp_row<8>(s_e, k0, d, m, z, Z, t, alpha, VAR, SV, AUX);
@@ -256,46 +272,86 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
       team_sync(bar_id, bar_n);
     }
 
-    // ---- posterior and hard decisions (Eq. s2e7)
-    if (act)
-      for (int w = z; w < words; w += Z) bits[w] = 0u;
+    // ---- posterior and hard decisions (Eq. s2e7), syndrome stop.  As in the CBP
+    // log-tanh kernel, the checks of one base row (the test row) are evaluated first;
+    // when one fails, the frame goes on without the full flush and syndrome scan.
     if (lane && z == 0) my->unsat = 0;
     team_sync(bar_id, bar_n);
-    for (int c = 0; c < p.nb; ++c) {
-      const uint2 ci = s_col[c];
-      const int cidx = ci.y & 0xffff;
-      const int sk = int(ci.x >> 16), rk = int(ci.x & 0xffff);
-      int v = 0;
-      bool neg = false;
-      if (act) {
+    if (act && p.stop == CBP_STOP_SYNDROME && t < p.max_iter) {
+      uint32_t par = 0;
+      const int tk0 = s_rptr[p.test_row], tk1 = s_rptr[p.test_row + 1];
+#pragma unroll 1
+      for (int k = tk0; k < tk1; ++k) {
+        const BaseEdge be = s_e[k];
+        const uint2 ci = s_col[be.c];
+        const int cidx = ci.y & 0xffff;
+        const int sk = int(ci.x >> 16), rk = int(ci.x & 0xffff);
         float q;
         int ck;
-        if (ci.y & 0x10000u) {  // weight-1 column: lane z owns its single check (rk, z)
+        if (ci.y & 0x10000u) {
           q = SV[cidx * Z + z];
           ck = rk * Z + z;
-          v = c * Z + mod_add(z + sk, Z);
         } else {
-          q = VAR[cidx * Z + z];
-          int zk = z - sk;
+          const int a = mod_add(z + be.s, Z);
+          q = VAR[cidx * Z + a];
+          int zk = a - sk;
           zk = zk < 0 ? zk + Z : zk;
           ck = rk * Z + zk;
-          v = c * Z + z;
         }
         float lb = q;
-        if (CBP) {  // flushed posterior: Eq. (s4e20) with the last check of v as c_j
+        if (CBP) {
           const float2 pc = CHK[ck];
           const float b1 = fabsf(pc.x);
           const float rm = __fmul_rn(alpha, (fabsf(q) == b1) ? pc.y : b1);
           lb = __fadd_rn(q, (sign_bit(pc.x) ^ (q < 0.0f)) ? -rm : rm);
         }
-        neg = lb < 0.0f;
-        if (p.soft) p.soft[static_cast<long long>(frame) * N + v] = lb;
+        par ^= lb < 0.0f ? 1u : 0u;
       }
-      warp_or_bit(bits + (v >> 5), neg ? (1u << (v & 31)) : 0u, act);
+      if (par) my->unsat = 1;
+    }
+    team_sync(bar_id, bar_n);
+    const bool full =
+        act && (t >= p.max_iter || (p.stop == CBP_STOP_SYNDROME &&
+                                    *static_cast<volatile int*>(&my->unsat) == 0));
+    // the decision bits are zero here (cleared at the start and after each full test);
+    // the warp skips the flush when none of its frames needs it
+    if (__any_sync(0xffffffffu, full)) {
+      for (int c = 0; c < p.nb; ++c) {
+        const uint2 ci = s_col[c];
+        const int cidx = ci.y & 0xffff;
+        const int sk = int(ci.x >> 16), rk = int(ci.x & 0xffff);
+        int v = 0;
+        bool neg = false;
+        if (full) {
+          float q;
+          int ck;
+          if (ci.y & 0x10000u) {  // weight-1 column: lane z owns its single check (rk, z)
+            q = SV[cidx * Z + z];
+            ck = rk * Z + z;
+            v = c * Z + mod_add(z + sk, Z);
+          } else {
+            q = VAR[cidx * Z + z];
+            int zk = z - sk;
+            zk = zk < 0 ? zk + Z : zk;
+            ck = rk * Z + zk;
+            v = c * Z + z;
+          }
+          float lb = q;
+          if (CBP) {  // flushed posterior: Eq. (s4e20) with the last check of v as c_j
+            const float2 pc = CHK[ck];
+            const float b1 = fabsf(pc.x);
+            const float rm = __fmul_rn(alpha, (fabsf(q) == b1) ? pc.y : b1);
+            lb = __fadd_rn(q, (sign_bit(pc.x) ^ (q < 0.0f)) ? -rm : rm);
+          }
+          neg = lb < 0.0f;
+          if (p.soft) p.soft[static_cast<long long>(frame) * N + v] = lb;
+        }
+        warp_or_bit(bits + (v >> 5), neg ? (1u << (v & 31)) : 0u, full);
+      }
     }
     team_sync(bar_id, bar_n);
     // ---- syndrome; a frame stops scanning at its first unsatisfied check row
-    if (act) {
+    if (full) {
       for (int r = 0; r < p.mb; ++r) {
         uint32_t pr = 0;
         for (int k = s_rptr[r]; k < s_rptr[r + 1]; ++k) {
@@ -309,7 +365,7 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
     }
     team_sync(bar_id, bar_n);
     bool done = false;
-    if (act) {
+    if (full) {
       const bool ok = my->unsat == 0;
       done = (ok && p.stop == CBP_STOP_SYNDROME) || t >= p.max_iter;
       if (done) {
@@ -319,6 +375,8 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
       }
     }
     team_sync(bar_id, bar_n);
+    if (full)  // ready for the next full test
+      for (int w = z; w < words; w += Z) bits[w] = 0u;
     if (act && z == 0) {
       if (done) {
         my->frame = frame + p.slots;
@@ -333,7 +391,10 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
 
 }  // namespace
 
-void* minsum_kernel_ptr(int alg, bool chk_shared) {
+void* minsum_kernel_ptr(int alg, bool chk_shared, bool rstore) {
+  if (alg == ALG_CBP_NMS && rstore)
+    return chk_shared ? reinterpret_cast<void*>(&minsum_kernel<ALG_CBP_NMS, true, 768, true>)
+                      : reinterpret_cast<void*>(&minsum_kernel<ALG_CBP_NMS, false, 768, true>);
   if (alg == ALG_CBP_NMS)
     return chk_shared ? reinterpret_cast<void*>(&minsum_kernel<ALG_CBP_NMS, true, 768>)
                       : reinterpret_cast<void*>(&minsum_kernel<ALG_CBP_NMS, false, 768>);

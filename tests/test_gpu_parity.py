@@ -117,6 +117,22 @@ def test_parity_26112_small_batch(large, alg):
     assert_parity(run_gpu(code, llr.cpu().numpy(), alg, max_iter=20), ref, alg)
 
 
+def test_cbp_nms_with_per_edge_messages(code576, large, monkeypatch):
+    """CBP min-sum with its C2V messages kept per edge (CBP_PLAN_NMS_R=1, the layout of the
+    log-tanh kernel) instead of rebuilt from (min1, min2, argmin, sign bits): bitwise equal
+    to the oracle, which keeps them per edge too."""
+    monkeypatch.setenv("CBP_PLAN_NMS_R", "1")
+    qc, code, oc = code576
+    fr = I.make_frames(qc, 700, 2.0, seed=1717)
+    ref = oc.decode(fr.llr, alg="cbp_nms", max_iter=30, threads=THREADS)
+    assert_parity(run_gpu(code, fr.llr, "cbp_nms"), ref, "cbp_nms per-edge R, 576")
+    qc, code, oc = large
+    llr, _ = I.make_frames_torch(qc, 96, 2.5, seed=2076)
+    ref = oc.decode(llr.cpu().numpy(), alg="cbp_nms", max_iter=20, threads=THREADS)
+    assert_parity(run_gpu(code, llr.cpu().numpy(), "cbp_nms", max_iter=20), ref,
+                  "cbp_nms per-edge R, 26112")
+
+
 def gpu_syndrome(qc, hard_bits):
     """H x^T on the GPU with torch gathers (independent of libcbp)."""
     rows = torch.from_numpy(np.stack([np.pad(r, (0, 32 - len(r)), constant_values=-1)
