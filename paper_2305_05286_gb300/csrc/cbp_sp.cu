@@ -16,7 +16,8 @@
 // A base row is processed in chunks of CH edges: the loads of a chunk are issued
 // together, then the CH edge updates run with independent phi evaluations, in
 // ascending column order (the order of the C2B fold).  While a row runs, one thread per
-// group asks L2 for the next row's C2V block (a bulk prefetch, no data dependence).
+// group asks L2 for the next row's C2V block and weight-1 state block (bulk prefetches,
+// no data dependence).
 //
 // Kernels of this file, all on the same sweep body (sp_body):
 //   cbp_sp_kernel        one code, frames spread over persistent frame slots
@@ -286,12 +287,20 @@ __device__ __forceinline__ void sweep_rows(int mb, bool any, const int* s_rptr,
       if (later && z == 0) {
         // the C2V slots of base row r + kPrefetchRows (cyclically) are contiguous in the
         // workspace: one bulk L2 prefetch per lane group brings them on chip while this
-        // row runs (a non-binding hint; rows in between may still rewrite those lines)
+        // row runs (a non-binding hint; rows in between may still rewrite those lines);
+        // likewise the (Q*, phi) block of that row's weight-1 column
         int rn = r + kPrefetchRows;
         rn = rn >= mb ? rn - mb : rn;
         const float* a = R + static_cast<long long>(s_rptr[rn]) * Z * FPT;
         const float* b = R + static_cast<long long>(s_rptr[rn + 1]) * Z * FPT;
         prefetch_l2(a, b);
+        if (FPT == 1) {  // and the state block of that row's weight-1 column, if any
+          const uint32_t x = s_spe[s_rptr[rn + 1] - 1].x;
+          if (x & kSpSelf) {
+            const float* sv = SV + 2 * static_cast<long long>(x & kSpMask);
+            prefetch_l2(sv, sv + 2 * Z);
+          }
+        }
       }
       float Sacc[FPT];
       uint32_t sig[FPT];
