@@ -53,7 +53,24 @@ OPS_SYN = 1
 # frame-sweep or edge-sweep.  Each entry names the kernel instance and the capture date,
 # and carries a hash of the kernel sources it was measured on: when the sources change,
 # the numbers are stale and the bench line reports null instead.
-CAPTURES = {}
+CAPTURES = {
+    "cbp_sp": {"kernel": "cbp_sp_kernel<0, 1, 3, 0, 768, 1>(KParams)", "date": "2026-12-04", "frames": 2432,
+               "sources": "dc04346ffe27882a", "dram_bytes_per_frame_sweep": 1392031,
+               "thread_inst_per_edge_sweep": 92.1, "issue_active": 0.523,
+               "warps_active_per_sm": 23.9},
+    "lbp_nms": {"kernel": "minsum_kernel<2, 0, 768, 0>(KParams)", "date": "2026-12-04", "frames": 2432,
+               "sources": "1ce95475ae5758a6", "dram_bytes_per_frame_sweep": 506329,
+               "thread_inst_per_edge_sweep": 73.1, "issue_active": 0.573,
+               "warps_active_per_sm": 22.6},
+    "cbp_nms": {"kernel": "minsum_kernel<1, 0, 768, 0>(KParams)", "date": "2026-12-04", "frames": 2432,
+               "sources": "1ce95475ae5758a6", "dram_bytes_per_frame_sweep": 848588,
+               "thread_inst_per_edge_sweep": 92.8, "issue_active": 0.578,
+               "warps_active_per_sm": 22.2},
+    "fbp_sp": {"kernel": "flood_kernel(KParams)", "date": "2026-12-04", "frames": 2432,
+               "sources": "60e20b4e44759bec", "dram_bytes_per_frame_sweep": 788498,
+               "thread_inst_per_edge_sweep": 109.7, "issue_active": 0.32,
+               "warps_active_per_sm": 12.0},
+}
 
 
 def load_peaks():
@@ -475,8 +492,11 @@ def run_sweep(args):
                                          alpha=args.alpha, workspace=ws)
             f()
             torch.cuda.synchronize()
+            # enough launches for the clock sampler (one sample per 200 ms) to see the load
+            first = timed_steps(torch, f, 1, stream)
+            steps = max(args.sweep_steps, int(np.ceil(args.sweep_min_ms / max(first, 1e-3))))
             with ClockSampler(gid) as clk:
-                ms = timed_steps(torch, f, args.sweep_steps, stream)
+                ms = timed_steps(torch, f, steps, stream)
                 torch.cuda.synchronize()
             st = frame_stats(torch, cbp, qc, hard, iters, cw)
             clocks = clk.summary()
@@ -486,7 +506,7 @@ def run_sweep(args):
                    "alg": alg, "alpha": args.alpha if "nms" in alg else None, "frames": B,
                    "max_iter": max_iter, "fer": st["fer"], "ber": st["ber"],
                    "mean_iters": st["mean_iters"], "gbps": K * B / (ms / 1e3) / 1e9,
-                   "ms_per_launch": ms, "launches": args.sweep_steps,
+                   "ms_per_launch": ms, "launches": steps,
                    "alu_frac": ro["frac"], "clocks": clocks}
             print(json.dumps(row), flush=True)
             del ws
@@ -764,6 +784,8 @@ def main():
                          "the 576-bit code)")
     ap.add_argument("--sweep-step", type=float, default=0.25)
     ap.add_argument("--sweep-steps", type=int, default=3, help="timed launches per point")
+    ap.add_argument("--sweep-min-ms", type=float, default=600.0,
+                    help="at least this long a timed region per point (more launches)")
     ap.add_argument("--sweep-max-iter", type=int, default=0,
                     help="0: 20 sweeps for the 26112-bit code, 30 for the 576-bit code")
     ap.add_argument("--sweep-algs", default="cbp_sp,cbp_nms,lbp_nms,fbp_sp")
