@@ -532,22 +532,35 @@ def run_learned(args):
     g = torch.Generator(device="cuda").manual_seed(5000)
     t0 = time.perf_counter()
     losses = []
+    stream = torch.cuda.current_stream()
+    step_ev = []  # CUDA events around the decoder's forward + loss and its backward
     for step in range(args.train_steps):
         ebn0 = 1.0 + 2.0 * torch.rand(B, generator=g, device="cuda")
         llr, cw = I.make_frames_torch(qc, B, ebn0, seed=5000 + step, zero_codeword=zero)
-        soft = cbp.weighted_cbp(code, llr, w, T, 2)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        # checkpoint spacing T: the forward records the tape, the backward recomputes nothing
+        soft = cbp.weighted_cbp(code, llr, w, T, T)
         loss = torch.nn.functional.binary_cross_entropy_with_logits(-soft, cw.float())
         opt.zero_grad(set_to_none=True)
+        ev[1].record(stream)
         loss.backward()
+        ev[2].record(stream)
         opt.step()
+        if step >= 3:  # after 3 warm-up steps
+            step_ev.append(ev)
         if step % 50 == 0 or step == args.train_steps - 1:
             losses.append((step, float(loss.item())))
             print(json.dumps({"train_step": step, "loss": losses[-1][1],
                               "elapsed_s": time.perf_counter() - t0}), flush=True)
     train_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    med = lambda xs: sorted(xs)[len(xs) // 2] if xs else None  # noqa: E731
+    step_ms = {"forward_loss": med([a.elapsed_time(b) for a, b, _ in step_ev]),
+               "backward": med([b.elapsed_time(c) for _, b, c in step_ev]),
+               "steps_timed": len(step_ev)}
     wl = w.detach().clone()
     ones = torch.ones_like(wl)
-    stream = torch.cuda.current_stream()
     rows = []
     chunk = min(args.eval_frames, 16384)
     for pi, e in enumerate((1.5, 2.0, 2.5)):
@@ -585,7 +598,8 @@ def run_learned(args):
     print(json.dumps({"code": args.learned_code, "zero_codeword": zero,
                       "learned_weights": wl.cpu().numpy().round(4).tolist(),
                       "train_steps": args.train_steps, "train_frames": B,
-                      "train_seconds": train_s, "loss_first_last": [losses[0], losses[-1]]}),
+                      "train_seconds": train_s, "train_step_ms_median": step_ms,
+                      "loss_first_last": [losses[0], losses[-1]]}),
           flush=True)
 
 

@@ -180,7 +180,11 @@ int cbp_launch_info(const cbp_code_t* code, int batch, const cbp_opts_t* opts, i
  * The paper has no weights; they follow the usual unrolled-decoder construction.
  *
  * Bytes of device workspace cbp_decode_weighted / cbp_decode_grad need for `batch` frames,
- * T sweeps and a state checkpoint every `ckpt_every` sweeps. */
+ * T sweeps and a state checkpoint every `ckpt_every` sweeps.  With ckpt_every = T the
+ * forward records the backward's tape of all T sweeps and keeps no checkpoint, so the
+ * backward recomputes nothing (the fastest backward; the tape takes 12 bytes per edge and
+ * sweep); with ckpt_every < T the backward recomputes each segment of ckpt_every sweeps
+ * from its checkpoint. */
 int cbp_grad_workspace_bytes(const cbp_code_t* code, int batch, int T, int ckpt_every,
                              size_t* bytes);
 
@@ -195,7 +199,8 @@ int cbp_decode_weighted(const cbp_code_t* code, const float* llr, const float* w
 /* Backward of cbp_decode_weighted (same code, llr, weights, T, ckpt_every, batch and the
  * workspace that forward call left): from grad_soft = dLoss/dsoft_out [batch][N], writes
  * grad_weights [T][mb] (summed over the frames) and, if not NULL, grad_llr [batch][N].
- * Reverse-mode through the sweeps in reverse order, each checkpoint segment recomputed;
+ * Reverse-mode through the sweeps in reverse order, each checkpoint segment recomputed
+ * (none when ckpt_every = T);
  * phi is differentiated as the evaluated cubic, |x| and the clamps with derivative 0 at
  * their kinks, signs as constants.  Summation order of the gradients is not fixed
  * (atomic adds). */

@@ -393,13 +393,18 @@ class _WeightedCBP(torch.autograd.Function):
 
 
 def weighted_cbp(code: Code, llr: torch.Tensor, weights: torch.Tensor, T: int,
-                 ckpt_every: int = 2) -> torch.Tensor:
+                 ckpt_every: int | None = None) -> torch.Tensor:
     """Differentiable weighted CBP: posterior LLRs [B, N] after T sweeps.
 
     ``weights`` [T, mb] scale the B2V messages per sweep and base row of the sending
     check (all ones = plain CBP with T sweeps).  Gradients flow to ``weights`` and
-    ``llr`` through the library's adjoint kernel."""
-    return _WeightedCBP.apply(llr, weights, code, int(T), int(ckpt_every))
+    ``llr`` through the library's adjoint kernel.  ``ckpt_every`` (default T): with T the
+    forward records the backward's tape of every sweep (12 bytes per edge and sweep of
+    workspace) and the backward recomputes nothing; a smaller value keeps a state
+    checkpoint every ``ckpt_every`` sweeps instead and the backward recomputes each
+    segment from it."""
+    ck = int(T) if ckpt_every is None else int(ckpt_every)
+    return _WeightedCBP.apply(llr, weights, code, int(T), ck)
 
 
 # ----------------------------------------------------------------------------- several codes

@@ -13,12 +13,15 @@
 // sweeps backwards (base rows descending, a check's edges descending), propagating
 // adjoints of Q*_v, phi(|Q*_v|), S_c and the C2V slots, and accumulating dLoss/dw.
 // The adjoint of phi is the derivative of the evaluated cubic (phi_deriv).
+// With one segment (ckpt = T) the forward records the tape of all T sweeps itself and
+// keeps no checkpoint; the backward then recomputes nothing.  The adjoints of the
+// check-beliefs live in shared memory when the CTA's frames' M floats each fit (GSS).
 //
 // Layout: F frames per CTA, Z lanes per frame (lane z owns check r*Z + z); all per-frame
 // arrays live in the workspace, frame-major:
 //   state   Q*[N] | phi[N] | S[M] (sign bit = sgn Omega) | R[E] ([base entry][lane])
 //   adjoint gQ[N] | gP[N] | gS[M] | gR[E]
-//   nseg checkpoints of the state
+//   nseg checkpoints of the state (none when nseg = 1)
 //   tape    d, sgn*mag, Q^new, each [ckpt][E]
 #include "cbp_internal.cuh"
 
@@ -48,7 +51,7 @@ __device__ __forceinline__ Frame frame_view(const GParams& p, long long f) {
   fr.gS = a + 2 * p.N;
   fr.gR = a + 2 * p.N + p.M;
   fr.ck = b + 2 * p.st_floats;
-  float* tp = fr.ck + static_cast<long long>(p.nseg) * p.st_floats;
+  float* tp = fr.ck + static_cast<long long>(p.nseg > 1 ? p.nseg : 0) * p.st_floats;
   const long long te = static_cast<long long>(p.ckpt) * p.E;
   fr.td = tp;
   fr.tm = tp + te;
@@ -63,6 +66,7 @@ struct Shared {
   uint2* col;  // (last row | shift << 16)
   float* gw;   // [T*mb] weight gradients of this CTA
   float* w;    // [T*mb] the weights
+  float* gs;   // [F][M] adjoints of the check-beliefs (backward with GSS)
 };
 
 __device__ Shared carve(unsigned char* smem, const GParams& p, bool load) {
@@ -79,6 +83,8 @@ __device__ Shared carve(unsigned char* smem, const GParams& p, bool load) {
   sh.gw = reinterpret_cast<float*>(sp);
   sp += sizeof(float) * p.T * p.mb;
   sh.w = reinterpret_cast<float*>(sp);
+  sp += sizeof(float) * p.T * p.mb;
+  sh.gs = reinterpret_cast<float*>(sp);
   if (load) {
     const int tid = threadIdx.x;
     for (int i = tid; i < kPhiSegments; i += blockDim.x) sh.tab[i] = p.phi_tab[i];
@@ -205,12 +211,14 @@ __global__ void __launch_bounds__(512) weighted_forward_kernel(const GParams p) 
     }
     if (bad) atomicOr(p.status, kStatusNonFiniteLlr);
   }
+  const bool one = p.nseg == 1;  // one segment: record the tape here, keep no checkpoint
   for (int s = 0; s < p.nseg; ++s) {
     const int t0 = s * p.ckpt + 1, t1 = min(p.T, (s + 1) * p.ckpt);
     __syncthreads();
-    if (act) copy_state(fr.ck + static_cast<long long>(s) * p.st_floats, fr.Q, p.st_floats, z, Z);
+    if (act && !one)
+      copy_state(fr.ck + static_cast<long long>(s) * p.st_floats, fr.Q, p.st_floats, z, Z);
     __syncthreads();
-    forward_sweeps(p, sh, fr, act, z, t0, t1, false);
+    forward_sweeps(p, sh, fr, act, z, t0, t1, one);
   }
   if (act) {  // flushed posterior, tau = T
     for (int c = 0; c < p.nb; ++c) {
@@ -228,6 +236,7 @@ __global__ void __launch_bounds__(512) weighted_forward_kernel(const GParams p) 
   }
 }
 
+template <bool GSS>
 __global__ void __launch_bounds__(512) weighted_backward_kernel(const GParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Shared sh = carve(smem, p, true);
@@ -237,8 +246,13 @@ __global__ void __launch_bounds__(512) weighted_backward_kernel(const GParams p)
   const bool act = f < p.F && frame < p.batch;
   const Frame fr = frame_view(p, act ? frame : 0);
   const float xlo = p.phi_xlo;
-  if (act)
+  // adjoints of this frame's check-beliefs
+  float* const gS = GSS ? sh.gs + static_cast<long long>(f < p.F ? f : 0) * p.M : fr.gS;
+  if (act) {
     for (long long i = z; i < p.st_floats; i += Z) fr.gQ[i] = 0.0f;  // all adjoints
+    if (GSS)
+      for (int i = z; i < p.M; i += Z) gS[i] = 0.0f;
+  }
   __syncthreads();
   // ---- adjoint of the flushed posterior (the state is the final one of the forward)
   for (int r = 0; r < p.mb; ++r) {
@@ -258,7 +272,7 @@ __global__ void __launch_bounds__(512) weighted_backward_kernel(const GParams p)
         gwx = gl * sgn * mag;
         const float gd =
             gl * sgn * w * phi_deriv(fabsf(d), xlo, sh.tab) * (d < 0.0f ? -1.0f : 1.0f);
-        fr.gS[m] += gd;
+        gS[m] += gd;
         fr.gP[v] = -gd;
       }
       if (be.flags & kLast) add_gw(sh, (p.T - 1) * p.mb + r, gwx);
@@ -268,17 +282,20 @@ __global__ void __launch_bounds__(512) weighted_backward_kernel(const GParams p)
   // ---- segments in reverse: recompute with the tape, then sweep backwards
   for (int s = p.nseg - 1; s >= 0; --s) {
     const int t0 = s * p.ckpt + 1, t1 = min(p.T, (s + 1) * p.ckpt);
-    if (act) copy_state(fr.Q, fr.ck + static_cast<long long>(s) * p.st_floats, p.st_floats, z, Z);
-    __syncthreads();
-    forward_sweeps(p, sh, fr, act, z, t0, t1, true);
+    if (p.nseg > 1) {  // one segment: the forward recorded the tape
+      if (act)
+        copy_state(fr.Q, fr.ck + static_cast<long long>(s) * p.st_floats, p.st_floats, z, Z);
+      __syncthreads();
+      forward_sweeps(p, sh, fr, act, z, t0, t1, true);
+    }
     for (int t = t1; t >= t0; --t) {
       const int ts = t - t0;
       for (int r = p.mb - 1; r >= 0; --r) {
         const int m = r * Z + z;
         float gSacc = 0.0f;
         if (act) {
-          gSacc = fr.gS[m];
-          fr.gS[m] = 0.0f;
+          gSacc = gS[m];
+          gS[m] = 0.0f;
         }
         const int k0 = sh.rptr[r];
         for (int kb = sh.rptr[r + 1] - 1; kb >= k0; kb -= kGradChunkAdj) {
@@ -344,7 +361,7 @@ __global__ void __launch_bounds__(512) weighted_backward_kernel(const GParams p)
                 const float sgn = smag < 0.0f ? -1.0f : 1.0f;
                 const float gd = gRn * sgn * w * phi_deriv(fabsf(d), xlo, sh.tab) *
                                  (d < 0.0f ? -1.0f : 1.0f);
-                atomicAdd(fr.gS + be.pr * Z + zjj[j], gd);  // d = |S_cj| - phi_v
+                atomicAdd(gS + be.pr * Z + zjj[j], gd);  // d = |S_cj| - phi_v
                 gpn = -gd;
               }
               fr.gP[v] = gpn;
@@ -368,7 +385,7 @@ __global__ void __launch_bounds__(512) weighted_backward_kernel(const GParams p)
 size_t grad_frame_floats(int N, int M, int E, int T, int ckpt) {
   const size_t st = (2 * static_cast<size_t>(N) + M + E + 3) & ~static_cast<size_t>(3);
   const size_t nseg = (T + ckpt - 1) / ckpt;
-  const size_t f = 2 * st + nseg * st + 3 * static_cast<size_t>(ckpt) * E;
+  const size_t f = 2 * st + (nseg > 1 ? nseg * st : 0) + 3 * static_cast<size_t>(ckpt) * E;
   return (f + 63) & ~static_cast<size_t>(63);
 }
 
@@ -376,7 +393,10 @@ cudaError_t grad_set_smem(int bytes) {
   cudaError_t e = cudaFuncSetAttribute(weighted_forward_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(weighted_backward_kernel,
+  e = cudaFuncSetAttribute(weighted_backward_kernel<true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(weighted_backward_kernel<false>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
@@ -388,7 +408,10 @@ cudaError_t launch_weighted_forward(const GParams& p, int grid, int threads, siz
 
 cudaError_t launch_weighted_backward(const GParams& p, int grid, int threads, size_t smem,
                                      cudaStream_t st) {
-  weighted_backward_kernel<<<grid, threads, smem, st>>>(p);
+  if (p.gs_shared)
+    weighted_backward_kernel<true><<<grid, threads, smem + p.gs_bytes, st>>>(p);
+  else
+    weighted_backward_kernel<false><<<grid, threads, smem, st>>>(p);
   return cudaGetLastError();
 }
 

@@ -967,6 +967,10 @@ int grad_setup(const cbp_code_t* c, int batch, int T, int ckpt, GParams* p, int*
   q.frame_floats = static_cast<long long>(ff);
   q.st_floats = static_cast<long long>((2 * static_cast<size_t>(c->N) + c->M + c->E + 3) &
                                        ~static_cast<size_t>(3));
+  // the backward keeps the check-belief adjoints in shared memory when they fit
+  const size_t gsb = sizeof(float) * static_cast<size_t>(F) * c->M;
+  q.gs_shared = sm + gsb <= static_cast<size_t>(di->smem_optin) ? 1 : 0;
+  q.gs_bytes = q.gs_shared ? static_cast<int>(gsb) : 0;
   *p = q;
   if (dio) *dio = di;
   return CBP_OK;

@@ -241,6 +241,8 @@ struct GParams {
   int Z, mb, nb, nnzb, N, M, E;
   int batch, T, ckpt, nseg, F;
   long long frame_floats, st_floats;
+  int gs_shared;         // backward: check-belief adjoints in shared memory (F * M floats)
+  int gs_bytes;          // their bytes, added to the launch's dynamic shared memory
 };
 size_t grad_frame_floats(int N, int M, int E, int T, int ckpt);
 cudaError_t launch_weighted_forward(const GParams& p, int grid, int threads, size_t smem,

@@ -2,7 +2,9 @@
 
 Forward: bit for bit equal to the FP32 oracle (same operations in the same order).
 Backward: the adjoint kernel's dLoss/dw and dLoss/dL against the oracle's reverse-mode
-adjoint (itself pinned by finite differences), relative to the largest component: 1e-3.
+adjoint (itself pinned by finite differences), relative to the largest component: 1e-3,
+both with checkpoint segments that the backward recomputes and with one segment
+(ckpt = T), whose tape the forward records.
 """
 import numpy as np
 import pytest
@@ -57,7 +59,7 @@ def test_unit_weights_equal_cbp(setup):
     assert np.array_equal(got, soft.cpu().numpy())
 
 
-@pytest.mark.parametrize("T,ckpt,ebn0", [(10, 2, 1.0), (4, 1, 0.5), (6, 4, 1.5)])
+@pytest.mark.parametrize("T,ckpt,ebn0", [(10, 2, 1.0), (4, 1, 0.5), (6, 4, 1.5), (8, 8, 1.0)])
 def test_adjoint_matches_oracle(setup, T, ckpt, ebn0):
     qc, code, oc = setup
     fr = I.make_frames(qc, 9, ebn0, seed=60 + T)
