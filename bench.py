@@ -277,7 +277,8 @@ def run_reference(args, rank):
 CODES = {"26112": ("code_26112", "QC-LDPC 46x68 base, Z=384"),
          "2304": ("code_2304", "QC-LDPC 12x24 base, Z=96"),
          "576": ("code_576", "QC-LDPC 12x24 base, Z=24"),
-         "peg2048": ("code_peg_2048", "regular (3,6) PEG code, Z=1")}
+         "peg2048": ("code_peg_2048", "regular (3,6) PEG code, Z=1"),
+         "pegirr2048": ("code_peg_irregular_2048", "irregular rate-1/2 PEG code, Z=1")}
 
 
 def bench_code(I, name):

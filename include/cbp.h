@@ -167,7 +167,10 @@ int cbp_decode_host(const cbp_code_t* code, const float* llr_host, uint32_t* har
  *   info[10] 1 if the frame-parallel CBP-SP kernel runs (one frame per thread; chosen when
  *            the lane-parallel plan would keep fewer than 128 lanes per SM busy, e.g. for
  *            Z = 1 codes, or cannot place a frame in shared memory)
- *   info[11] reserved (0)
+ *   info[11] 1 if the wavefront-schedule CBP-SP kernel runs (the checks of each level of
+ *            the expanded graph's dependency order on parallel lanes, one group per frame;
+ *            chosen before the frame-parallel kernel where a frame's state fits in shared
+ *            memory)
  * `info` is a host array of 12 ints.  Nothing is launched. */
 int cbp_launch_info(const cbp_code_t* code, int batch, const cbp_opts_t* opts, int* info);
 

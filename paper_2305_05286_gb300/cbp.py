@@ -192,7 +192,7 @@ class Code:
         _check("cbp_launch_info", lib().cbp_launch_info(self._h, int(batch), C.byref(o), info))
         keys = ("frames_per_sm", "threads_per_cta", "ctas_per_sm", "lane_groups_per_cta",
                 "frames_per_lane_group", "check_state_shared", "ctas", "team_lane_groups",
-                "shared_bytes", "weight1_last", "frame_parallel")
+                "shared_bytes", "weight1_last", "frame_parallel", "level_schedule")
         return dict(zip(keys, list(info)))
 
     # ------------------------------------------------------------------ decode

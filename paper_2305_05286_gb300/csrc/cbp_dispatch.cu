@@ -7,6 +7,7 @@ static void* select_kernel(const Variant& v) {
   switch (v.alg) {
     case ALG_CBP_SP:
       if (v.fp) return fp_kernel_ptr();
+      if (v.lvl) return level_kernel_ptr(v.shrec);
       return v.win ? sp_win_kernel_ptr(v.chk_shared)
                    : sp_kernel_ptr(v.chk_shared, v.fpt, v.wide, v.self_last);
     case ALG_CBP_NMS:

@@ -112,6 +112,8 @@ int device_init(int dev, DeviceInfo** out) {
                            {ALG_CBP_SP, true, 1, false, false, true},
                            {ALG_CBP_SP, false, 1, false, false, true},
                            {ALG_CBP_SP, false, 1, false, false, false, true},
+                           {ALG_CBP_SP, false, 1, false, false, false, false, false, true},
+                           {ALG_CBP_SP, false, 1, false, false, false, false, false, true, true},
                            {ALG_CBP_NMS, true, 1}, {ALG_CBP_NMS, false, 1},
                            {ALG_CBP_NMS, true, 1, false, false, false, false, true},
                            {ALG_CBP_NMS, false, 1, false, false, false, false, true},
@@ -228,6 +230,8 @@ struct cbp_code {
   int test_row = 0;          // a base row of the largest degree (the sweep-end pre-test)
   int ncomp = 0, nself = 0;  // columns of weight >= 2 / of weight 1
   bool self_last = true;     // every row holds at most one weight-1 entry, as its last
+  int nlev = 0;              // levels of the wavefront schedule (0: tables not built)
+  int lvl_maxw = 0;          // checks in its widest level
   CodeDev d;
   Shape shape() const {
     return Shape{Z, N, M, E, nnzb, mb, nb, (N + 31) / 32, ncomp, nself};
@@ -283,6 +287,7 @@ struct Plan {
   size_t ws_bytes = 0;
   // frame-parallel kernel (v.fp): slots and workspace offsets, see KParams
   long long fp_slots = 0, fp_off_sv = 0, fp_off_s = 0, fp_off_r = 0, fp_off_b = 0;
+  int lvl_lanes = 0;  // wavefront-schedule kernel (v.lvl): lanes per group
 };
 
 // CBP-SP takes the frame-parallel kernel when the lane-parallel plan keeps fewer lanes
@@ -323,6 +328,59 @@ int make_fp_plan(const cbp_code* c, const DeviceInfo& di, int batch, Plan* out) 
   pl.fp_off_r = take(c->E);
   pl.fp_off_b = take((c->N + 31) / 32);
   pl.ws_bytes = static_cast<size_t>(off) * sizeof(float);
+  *out = pl;
+  return CBP_OK;
+}
+
+// Launch plan of the wavefront-schedule kernel, one CTA per SM: as many lane groups (one
+// frame each) as shared memory holds (a frame's Q*/phi, check-beliefs and decision bits;
+// at most 15, one named barrier each), then the widest group of whole warps that keeps
+// the CTA within its thread limit, but no wider than the widest level (CBP_LVL_LANES =
+// 32..256 in the environment for tuning); fewer groups for small batches.  The workspace
+// holds each group slot's C2V messages.  The edge records go to shared memory too when
+// the code has the 8-byte form and a frame still fits (CBP_LVL_SHREC=0 keeps them in
+// global memory).
+int make_level_plan(const cbp_code* c, const DeviceInfo& di, int batch, Plan* out) {
+  if (c->nlev == 0) return CBP_EUNSUPPORTED;
+  Plan pl;
+  pl.v = Variant{ALG_CBP_SP, false, 1};
+  pl.v.lvl = true;
+  size_t fixed = sizeof(float4) * kPhiSegments + sizeof(int) * 16;
+  const size_t fr_floats = 2 * static_cast<size_t>(c->N) + align4(c->M) +
+                           align4((static_cast<size_t>(c->N) + 31) / 32);
+  const size_t avail = static_cast<size_t>(di.smem_optin);
+  const size_t recb = sizeof(uint2) * static_cast<size_t>(c->E) + sizeof(int) * align4(c->M + 1);
+  const char* es = std::getenv("CBP_LVL_SHREC");
+  if (c->d.lvl_rec8 && !(es && es[0] == '0') && fixed + recb + fr_floats * 4 <= avail) {
+    pl.v.shrec = true;
+    fixed += recb;
+  }
+  if (fixed + fr_floats * 4 > avail) return CBP_EUNSUPPORTED;
+  int F = static_cast<int>(std::min<size_t>((avail - fixed) / (fr_floats * 4), 15));
+  int G = std::max(32, std::min((level_max_threads() / F) / 32 * 32,
+                                (c->lvl_maxw + 31) / 32 * 32));
+  if (const char* e = std::getenv("CBP_LVL_LANES")) {
+    const int g = std::atoi(e);
+    if (g >= 32 && g <= 256 && g % 32 == 0) G = g;
+  }
+  F = std::min(F, level_max_threads() / G);
+  const int spread = std::max(1, (batch + di.sms - 1) / di.sms);
+  F = std::max(1, std::min(F, spread));
+  pl.F = F;
+  pl.threads = F * G;
+  pl.smem = fixed + static_cast<size_t>(F) * fr_floats * 4;
+  int ctas = 0;
+  if (decoder_occupancy(pl.v, pl.threads, pl.smem, &ctas) != cudaSuccess) return CBP_ECUDA;
+  if (ctas < 1) return CBP_EUNSUPPORTED;
+  const long long need = (static_cast<long long>(batch) + F - 1) / F;
+  pl.grid = static_cast<int>(std::max(1LL, std::min<long long>(need, 1LL * di.sms * ctas)));
+  pl.team_groups = 1;
+  pl.ctas_per_sm = ctas;
+  pl.frames_per_sm = ctas * F;
+  pl.sh_frame = static_cast<int>(fr_floats);
+  pl.lvl_lanes = G;
+  pl.ws.slot = static_cast<long long>(align64(static_cast<size_t>(c->E)));
+  pl.ws_bytes = static_cast<size_t>(pl.grid) * F * static_cast<size_t>(pl.ws.slot) * sizeof(float);
   *out = pl;
   return CBP_OK;
 }
@@ -450,16 +508,28 @@ int make_lane_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, 
 // where the lane-parallel plan would leave the SMs' lanes idle (CBP_PLAN_FP=0/1 in the
 // environment forces either; the paper-literal stop and the no-alloc entry point always
 // run lane-parallel).
+// CBP-SP where the lane-parallel plan keeps fewer than kFpMinLanes lanes per SM busy (or
+// has none): the wavefront-schedule kernel when its tables exist and a frame fits, else
+// the frame-parallel kernel.  CBP_PLAN_FP=1 / CBP_PLAN_LEVEL=1 force one of them,
+// CBP_PLAN_FP=0 keeps the lane-parallel plan, CBP_PLAN_LEVEL=0 skips the wavefront kernel.
 int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan* out,
               int stop = CBP_STOP_SYNDROME, bool allow_fp = true) {
   const bool sp = alg == ALG_CBP_SP && stop != CBP_STOP_WINDOW && allow_fp;
   const char* e = sp ? std::getenv("CBP_PLAN_FP") : nullptr;
+  const char* el = sp ? std::getenv("CBP_PLAN_LEVEL") : nullptr;
   if (e && e[0] == '1') return make_fp_plan(c, di, batch, out);
+  if (el && el[0] == '1') return make_level_plan(c, di, batch, out);
   const int rc = make_lane_plan(c, di, alg, batch, out, stop);
   if (!sp || (e && e[0] == '0')) return rc;
   if (rc == CBP_EUNSUPPORTED ||
-      (rc == CBP_OK && 1LL * out->frames_per_sm * c->Z < kFpMinLanes))
+      (rc == CBP_OK && 1LL * out->frames_per_sm * c->Z < kFpMinLanes)) {
+    Plan lp;
+    if (!(el && el[0] == '0') && make_level_plan(c, di, batch, &lp) == CBP_OK) {
+      *out = lp;
+      return CBP_OK;
+    }
     return make_fp_plan(c, di, batch, out);
+  }
   return rc;
 }
 
@@ -505,6 +575,13 @@ KParams code_params(const cbp_code* c, const DeviceInfo& di, const Plan& pl, int
   p.fp_off_s = pl.fp_off_s;
   p.fp_off_r = pl.fp_off_r;
   p.fp_off_b = pl.fp_off_b;
+  p.lvl_ptr = c->d.lvl_ptr;
+  p.lvl_e0 = c->d.lvl_e0;
+  p.lvl_edge = c->d.lvl_edge;
+  p.lvl_rec8 = c->d.lvl_rec8;
+  p.last_chk = c->d.last_chk;
+  p.nlev = c->nlev;
+  p.lvl_lanes = pl.lvl_lanes;
   return p;
 }
 
@@ -526,6 +603,96 @@ int check_opts(const cbp_opts_t* o, int* alg, float* alpha, int* stop, float** s
   *stop = o->stop_mode;
   *soft = o->soft_out;
   if (*soft && !aligned(*soft, 4)) return CBP_EINVAL;
+  return CBP_OK;
+}
+
+// Largest expanded edge count for which the wavefront schedule is built (16 MB of records).
+constexpr long long kLvlMaxEdges = 1 << 20;
+
+// The wavefront schedule of the expanded graph: checks m = r*Z + z in the paper's order,
+// the variables of a check in ascending base column.  level(m) = 1 + the largest level of
+// the previous check (in that order) of each of m's variables, 0 if there is none; checks
+// are listed by level, then index, and their edges renumbered in that order.
+int build_level_tables(cbp_code* c, const std::vector<BaseEdge>& edges,
+                       const std::vector<int>& rptr) {
+  const int Z = c->Z, M = c->M, N = c->N, E = c->E;
+  std::vector<int> ep(M + 1, 0), ev(E), echk(E);
+  std::vector<int> colw(c->nb, 0);
+  for (const BaseEdge& be : edges) ++colw[be.c];
+  for (int r = 0, e = 0; r < c->mb; ++r)
+    for (int z = 0; z < Z; ++z) {
+      const int m = r * Z + z;
+      ep[m] = e;
+      for (int k = rptr[r]; k < rptr[r + 1]; ++k) {
+        ev[e] = edges[k].c * Z + (z + edges[k].s) % Z;
+        echk[e] = m;
+        ++e;
+      }
+      ep[m + 1] = e;
+    }
+  std::vector<int> level(M, 0), pred(E, -1), last_e(N, -1);
+  int nlev = 0;
+  for (int m = 0; m < M; ++m) {
+    int lv = 0;
+    for (int e = ep[m]; e < ep[m + 1]; ++e)
+      if (last_e[ev[e]] >= 0) lv = std::max(lv, level[echk[last_e[ev[e]]]] + 1);
+    level[m] = lv;
+    nlev = std::max(nlev, lv + 1);
+    for (int e = ep[m]; e < ep[m + 1]; ++e) {
+      pred[e] = last_e[ev[e]];
+      last_e[ev[e]] = e;
+    }
+  }
+  std::vector<int> lptr(nlev + 1, 0), order(M), newidx(E);
+  for (int m = 0; m < M; ++m) ++lptr[level[m] + 1];
+  for (int l = 0; l < nlev; ++l) c->lvl_maxw = std::max(c->lvl_maxw, lptr[l + 1]);
+  for (int l = 0; l < nlev; ++l) lptr[l + 1] += lptr[l];
+  {
+    std::vector<int> fill(lptr.begin(), lptr.end() - 1);
+    for (int m = 0; m < M; ++m) order[fill[level[m]]++] = m;
+  }
+  std::vector<int> e0(M + 1), cpos(M);
+  for (int ci = 0, e2 = 0; ci < M; ++ci) {
+    const int m = order[ci];
+    cpos[m] = ci;
+    e0[ci] = e2;
+    for (int e = ep[m]; e < ep[m + 1]; ++e) newidx[e] = e2++;
+  }
+  e0[M] = E;
+  const bool small = M <= 4096 && E < (1 << 20);  // the 8-byte record form
+  std::vector<LvlEdge> rec(E);
+  std::vector<uint2> rec8(small ? E : 0);
+  for (int e = 0; e < E; ++e) {
+    const int v = ev[e];
+    const bool first = pred[e] < 0;
+    const int pe = first ? last_e[v] : pred[e];  // cyclically: the last check of v
+    const uint32_t x = static_cast<uint32_t>(v) | (first ? kSpFirst : 0u) |
+                       (colw[v / Z] == 1 ? kSpSelf : 0u);
+    const uint32_t cj = static_cast<uint32_t>(cpos[echk[pe]]);
+    const uint32_t pn = static_cast<uint32_t>(newidx[pe]);
+    rec[newidx[e]] = make_uint4(x, cj, pn, 0u);
+    if (small) rec8[newidx[e]] = make_uint2(x, pn | (cj << 20));
+  }
+  std::vector<int> lastc(N);
+  for (int v = 0; v < N; ++v) lastc[v] = cpos[echk[last_e[v]]];
+  bool ok = cudaMalloc(&c->d.lvl_ptr, sizeof(int) * lptr.size()) == cudaSuccess &&
+            cudaMalloc(&c->d.lvl_e0, sizeof(int) * e0.size()) == cudaSuccess &&
+            cudaMalloc(&c->d.lvl_edge, sizeof(LvlEdge) * rec.size()) == cudaSuccess &&
+            (!small || cudaMalloc(&c->d.lvl_rec8, sizeof(uint2) * rec8.size()) == cudaSuccess) &&
+            cudaMalloc(&c->d.last_chk, sizeof(int) * lastc.size()) == cudaSuccess;
+  if (!ok) return CBP_ENOMEM;
+  ok = cudaMemcpy(c->d.lvl_ptr, lptr.data(), sizeof(int) * lptr.size(),
+                  cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(c->d.lvl_e0, e0.data(), sizeof(int) * e0.size(), cudaMemcpyHostToDevice) ==
+           cudaSuccess &&
+       cudaMemcpy(c->d.lvl_edge, rec.data(), sizeof(LvlEdge) * rec.size(),
+                  cudaMemcpyHostToDevice) == cudaSuccess &&
+       (!small || cudaMemcpy(c->d.lvl_rec8, rec8.data(), sizeof(uint2) * rec8.size(),
+                             cudaMemcpyHostToDevice) == cudaSuccess) &&
+       cudaMemcpy(c->d.last_chk, lastc.data(), sizeof(int) * lastc.size(),
+                  cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) return CBP_ECUDA;
+  c->nlev = nlev;
   return CBP_OK;
 }
 
@@ -669,6 +836,12 @@ int cbp_code_create(const int32_t* base, int mb, int nb, int Z, cbp_code_t** out
     cbp_code_destroy(c);
     return CBP_ECUDA;
   }
+  if (1LL * nnzb * Z <= kLvlMaxEdges) {
+    if (int rc = build_level_tables(c, edges, rptr)) {
+      cbp_code_destroy(c);
+      return rc;
+    }
+  }
   *out = c;
   return CBP_OK;
 }
@@ -681,6 +854,11 @@ void cbp_code_destroy(cbp_code_t* c) {
   cudaFree(c->d.rptr);
   cudaFree(c->d.cols);
   cudaFree(c->d.cptr);
+  cudaFree(c->d.lvl_ptr);
+  cudaFree(c->d.lvl_e0);
+  cudaFree(c->d.lvl_edge);
+  cudaFree(c->d.lvl_rec8);
+  cudaFree(c->d.last_chk);
   delete c;
 }
 
@@ -736,7 +914,7 @@ int cbp_launch_info(const cbp_code_t* c, int batch, const cbp_opts_t* opts, int*
   info[8] = static_cast<int>(pl.smem);
   info[9] = pl.v.self_last ? 1 : 0;
   info[10] = pl.v.fp ? 1 : 0;
-  info[11] = 0;
+  info[11] = pl.v.lvl ? 1 : 0;
   return CBP_OK;
 }
 

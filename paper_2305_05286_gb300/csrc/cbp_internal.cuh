@@ -112,8 +112,18 @@ __device__ __forceinline__ bool non_finite(float x) {
   return (__float_as_uint(x) & 0x7f800000u) == 0x7f800000u;
 }
 
+// Edge record of the wavefront-schedule kernel (cbp_level.cu), checks and edges in level
+// order: x = v | kSpFirst (first check of v) | kSpSelf (v has one check), y = the
+// predecessor check of v (cyclically), z = the predecessor's edge to v.
+using LvlEdge = uint4;
+
 struct CodeDev {
   uint32_t* status = nullptr;  // [2]: live flags, last value taken by cbp_device_status
+  int* lvl_ptr = nullptr;      // [nlev + 1] wavefront schedule (null when not built)
+  int* lvl_e0 = nullptr;       // [M + 1] first edge of each level-ordered check
+  LvlEdge* lvl_edge = nullptr;  // [E]
+  uint2* lvl_rec8 = nullptr;   // [E] 8-byte records (M <= 4096, E < 2^20), else null
+  int* last_chk = nullptr;     // [N] the last check of each variable (level order)
   BaseEdge* edges = nullptr;  // [nnzb]
   SpEdge* spe = nullptr;      // [nnzb], CBP-SP kernel records
   int* rptr = nullptr;        // [mb + 1]
@@ -154,6 +164,14 @@ struct KParams {
   // frame-parallel CBP-SP (cbp_fp.cu): frame slots of the launch (one per thread) and the
   // offsets (floats) of SV, S, R and the decision bits in the workspace; QP is at 0
   long long fp_slots, fp_off_sv, fp_off_s, fp_off_r, fp_off_b;
+  // wavefront-schedule CBP-SP (cbp_level.cu): the code's level tables, the number of
+  // levels and the lanes of a group
+  const int* lvl_ptr;
+  const int* lvl_e0;
+  const LvlEdge* lvl_edge;
+  const uint2* lvl_rec8;
+  const int* last_chk;
+  int nlev, lvl_lanes;
 };
 
 // Several codes in one launch (CBP-SP): per-code parameters and the chunk list.
@@ -185,6 +203,8 @@ struct Variant {
   bool self_last = false;  // CBP-SP, one frame per group: every weight-1 edge ends its row
   bool fp = false;         // CBP-SP, frame-parallel kernel: one frame per thread
   bool rstore = false;     // CBP min-sum: C2V messages kept per edge (no rebuild)
+  bool lvl = false;        // CBP-SP on the wavefront schedule of the expanded graph
+  bool shrec = false;      // that kernel with its 8-byte edge records in shared memory
 };
 
 // Sizes that fix the shared-memory and workspace layout of a launch.
@@ -206,6 +226,8 @@ cudaError_t decoder_func_attrs(const Variant& v, cudaFuncAttributes* a);
 cudaError_t decoder_set_smem(const Variant& v, int bytes);
 cudaError_t decoder_occupancy(const Variant& v, int threads, size_t smem, int* ctas);
 void* sp_kernel_ptr(bool chk_shared, int fpt, bool wide, bool self_last);  // cbp_sp.cu
+void* level_kernel_ptr(bool shrec);  // cbp_level.cu
+int level_max_threads();
 void* sp_multi_kernel_ptr(bool chk_shared, int fpt, bool self_last);  // cbp_sp.cu
 void* sp_win_kernel_ptr(bool chk_shared);                   // cbp_sp.cu
 cudaError_t launch_multi(bool chk_shared, int fpt, bool self_last, const MultiParams& mp, int grid,

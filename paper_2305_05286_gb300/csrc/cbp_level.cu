@@ -1,0 +1,223 @@
+// CBP, log-tanh form (Sec. IV-C, Steps 1-3), on a wavefront schedule of the expanded
+// Tanner graph: the kernel for codes with small lifting sizes (down to Z = 1, codes given
+// as plain parity-check matrices such as PEG codes), where the Z checks of a base row are
+// too few to fill the lanes of the lane-parallel kernel.
+//
+// The paper's order visits the checks m = 0, 1, ..., M-1 one after another.  A check only
+// depends on the checks before it that share one of its variables (it reads their
+// (Q*, phi) and check-beliefs and writes their C2V slots).  The host gives every check the
+// level 1 + max(level of the previous check of each of its variables), 0 if none, so the
+// checks of one level share no variable and none is another's predecessor.  Running the
+// levels in order, each level's checks in any order, gives every check exactly the inputs
+// it has in the sequential order: the result is that order's, bit for bit.  (A QC code's
+// base row is such a level; a random PEG code with N = 2048 has 24 levels per sweep.)
+//
+// A CTA holds F lane groups of G lanes (whole warps); each group decodes one frame at a
+// time.  Lane l takes the checks l, l + G, ... of a level; a named barrier over the group
+// ends the level.  Checks are numbered in level order (ci).  Per group, shared memory
+// holds the frame's state:
+//   QP   (Q*_v, phi(|Q*_v|)) for every variable                     [N]
+//   S    check-beliefs, sign bit = sgn Omega, by level-ordered check  [M]
+//   bits decisions of the flushed posterior                          [words]
+// and the workspace the C2V messages R, indexed by the level-ordered edge, so the own
+// slots of a check are contiguous.  Level-ordered tables (host-built):
+//   lvl_ptr  [L + 1]  level l holds the checks [lvl_ptr[l], lvl_ptr[l + 1])
+//   lvl_e0   [M + 1]  first edge of each check; the next entry ends it
+//   lvl_edge [E]      (v | first << 30 | self << 31, predecessor check, predecessor edge)
+//   lvl_rec8 [E]      the same in 8 bytes (v | flags, predecessor edge | check << 20), when
+//                     M <= 4096 and E < 2^20; SHREC instances copy it and lvl_e0 into
+//                     shared memory instead of reading lvl_edge through L1
+//   last_chk [N]      the last check of each variable (flushed posterior)
+// The per-edge arithmetic is the lane-parallel kernel's, operation for operation.
+#include "cbp_kernel_common.cuh"
+
+namespace cbp {
+namespace {
+
+constexpr int kLvlChunk = 3;        // edges of a check whose loads are issued together
+constexpr int kLvlMaxThreads = 768;
+
+// One edge record: variable and flags, predecessor check, predecessor edge.
+struct LvlRec {
+  uint32_t vx;
+  int cj, pe;
+};
+
+template <bool SHREC>
+__device__ __forceinline__ LvlRec lvl_rec(const uint2* s_rec, const LvlEdge* __restrict__ led,
+                                          int e) {
+  LvlRec r;
+  if (SHREC) {
+    const uint2 a = s_rec[e];
+    r.vx = a.x;
+    r.cj = static_cast<int>(a.y >> 20);
+    r.pe = static_cast<int>(a.y & 0xFFFFFu);
+  } else {
+    const uint4 a = __ldg(led + e);
+    r.vx = a.x;
+    r.cj = static_cast<int>(a.y);
+    r.pe = static_cast<int>(a.z);
+  }
+  return r;
+}
+
+template <bool SHREC>
+__global__ void __launch_bounds__(kLvlMaxThreads, 1) cbp_level_kernel(const KParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int G = p.lvl_lanes, F = p.F;
+  const int N = p.N, M = p.M, E = p.E, words = p.words;
+  const int tid = threadIdx.x;
+  const int g = tid / G, l = tid - g * G;
+  unsigned char* sp = smem;
+  float4* s_tab = reinterpret_cast<float4*>(sp);
+  sp += sizeof(float4) * kPhiSegments;
+  int* s_unsat = reinterpret_cast<int*>(sp);  // per group: a check of the frame fails
+  sp += sizeof(int) * 16;
+  uint2* s_rec = reinterpret_cast<uint2*>(sp);
+  int* s_e0 = reinterpret_cast<int*>(sp + sizeof(uint2) * E);
+  if (SHREC) sp += sizeof(uint2) * E + sizeof(int) * ((M + 1 + 3) & ~3);
+  for (int i = tid; i < kPhiSegments; i += blockDim.x) s_tab[i] = p.phi_tab[i];
+  if (tid < 16) s_unsat[tid] = 0;
+  if (SHREC) {
+    for (int i = tid; i < E; i += blockDim.x) s_rec[i] = p.lvl_rec8[i];
+    for (int i = tid; i <= M; i += blockDim.x) s_e0[i] = p.lvl_e0[i];
+  }
+  __syncthreads();
+  if (g >= F) return;
+  const int* e0t = SHREC ? s_e0 : p.lvl_e0;
+  const LvlEdge* __restrict__ led = p.lvl_edge;
+  float* gb = reinterpret_cast<float*>(sp) + static_cast<size_t>(g) * p.sh_frame;
+  float2* QP = reinterpret_cast<float2*>(gb);
+  float* S = gb + 2 * static_cast<size_t>(N);
+  uint32_t* bits = reinterpret_cast<uint32_t*>(S + ((M + 3) & ~3));
+  const long long slot = static_cast<long long>(blockIdx.x) * F + g;
+  float* R = p.ws + slot * p.ws_slot;
+  const float4* tab = s_tab;
+  const float xlo = p.phi_xlo;
+  const int bar_id = 1 + g;
+
+  for (long long frame = slot; frame < p.batch; frame += p.slots) {
+    // ---- Step 1, Eq. (s4e15): Q*_v = L_v (+0 turns -0 into +0)
+    const float* src = p.llr + frame * N;
+    bool bad = false;
+    for (int v = l; v < N; v += G) {
+      const float L = __fadd_rn(__ldg(src + v), 0.0f);
+      bad |= non_finite(L);
+      QP[v].x = L;
+    }
+    if (bad) atomicOr(p.status, kStatusNonFiniteLlr);
+    team_sync(bar_id, G);
+
+    for (int t = 1;; ++t) {
+      // ---- Step 2: the levels in order, a level's checks on the lanes
+      for (int lv = 0; lv < p.nlev; ++lv) {
+        const int i1 = p.lvl_ptr[lv + 1];
+        for (int ci = p.lvl_ptr[lv] + l; ci < i1; ci += G) {
+          const int e1 = e0t[ci + 1];
+          float Sacc = 0.0f;
+          uint32_t sig = 0;
+          for (int eb = e0t[ci]; eb < e1; eb += kLvlChunk) {
+            float q[kLvlChunk], ph[kLvlChunk], sj[kLvlChunk], ro[kLvlChunk];
+            uint32_t vx[kLvlChunk];
+            int pe[kLvlChunk];
+#pragma unroll
+            for (int j = 0; j < kLvlChunk; ++j) {  // loads of the chunk
+              const int e = eb + j;
+              if (e < e1) {
+                const LvlRec rec = lvl_rec<SHREC>(s_rec, led, e);
+                vx[j] = rec.vx;
+                pe[j] = rec.pe;
+                const float2 qp = QP[rec.vx & kSpMask];
+                q[j] = qp.x;
+                ph[j] = qp.y;
+                sj[j] = S[rec.cj];
+                ro[j] = (!(rec.vx & kSpSelf) && t > 1) ? R[e] : 0.0f;
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < kLvlChunk; ++j) {  // the updates, in column order
+              if (eb + j < e1) {
+                const bool self = vx[j] & kSpSelf;
+                // B2V, Eqs. (s4e18), (s4e13); a variable not visited before adds no C2V
+                const float mag = phi_eval(fabsf(__fsub_rn(fabsf(sj[j]), ph[j])), xlo, tab);
+                const float rb = __uint_as_float(
+                    __float_as_uint(mag) |
+                    ((__float_as_uint(sj[j]) ^ __float_as_uint(q[j])) & 0x80000000u));
+                const bool first = (t == 1) && (vx[j] & kSpFirst);
+                const float Rn = first ? 0.0f : rb;
+                // V2C, Eqs. (s4e20), (s4e19); weight-1 column: c_j == c_i
+                const float rold = self ? Rn : ro[j];
+                const float qn = __fsub_rn(__fadd_rn(q[j], Rn), rold);
+                // C2B, Eq. (s4e21) as a sum of phi; the sign bits fold into sig
+                const float phn = phi_eval(fabsf(qn), xlo, tab);
+                Sacc = __fadd_rn(Sacc, phn);
+                sig ^= __float_as_uint(qn);
+                if (!self && !first) R[pe[j]] = Rn;  // R_{c_j->v} <- R^new, Eq. (s4e22)
+                QP[vx[j] & kSpMask] = make_float2(qn, phn);
+              }
+            }
+          }
+          // Eq. (s4e23); the sign bit carries sgn(Omega)
+          S[ci] = __uint_as_float(__float_as_uint(Sacc) | (sig & 0x80000000u));
+        }
+        team_sync(bar_id, G);
+      }
+      // ---- flushed posterior (Eq. s4e20 with the last check of v, read-only) and the
+      // decisions (Eq. s2e7): lane l takes v = l, l + G, ...; a warp's 32 variables of one
+      // step are one aligned word
+      for (int vb = 0; vb < N; vb += G) {
+        const int v = vb + l;
+        bool neg = false;
+        if (v < N) {
+          const float2 qp = QP[v];
+          const float Sk = S[__ldg(p.last_chk + v)];
+          const float mag = phi_eval(fabsf(__fsub_rn(fabsf(Sk), qp.y)), xlo, tab);
+          const float lb = __fadd_rn(
+              qp.x, __uint_as_float(__float_as_uint(mag) |
+                                    ((__float_as_uint(Sk) ^ __float_as_uint(qp.x)) &
+                                     0x80000000u)));
+          neg = lb < 0.0f;
+          if (p.soft) p.soft[frame * N + v] = lb;
+        }
+        const unsigned wv = __ballot_sync(0xffffffffu, neg);
+        if ((l & 31) == 0 && v < N) bits[v >> 5] = wv;
+      }
+      team_sync(bar_id, G);
+      // ---- syndrome: every check's parity over its variables' decisions
+      bool fail = false;
+      for (int ci = l; ci < M; ci += G) {
+        uint32_t par = 0;
+        const int e1 = e0t[ci + 1];
+        for (int e = e0t[ci]; e < e1; ++e) {
+          const uint32_t v = lvl_rec<SHREC>(s_rec, led, e).vx & kSpMask;
+          par ^= bits[v >> 5] >> (v & 31);
+        }
+        fail |= (par & 1u) != 0;
+      }
+      if (fail) s_unsat[g] = 1;
+      team_sync(bar_id, G);
+      const bool ok = *static_cast<volatile int*>(&s_unsat[g]) == 0;
+      const bool done = (ok && p.stop == CBP_STOP_SYNDROME) || t >= p.max_iter;
+      if (done) {  // Step 3
+        uint32_t* ho = p.hard + frame * words;
+        for (int w = l; w < words; w += G) ho[w] = bits[w];
+        if (l == 0) p.iters[frame] = ok ? t : -t;
+      }
+      team_sync(bar_id, G);
+      if (l == 0) s_unsat[g] = 0;
+      team_sync(bar_id, G);
+      if (done) break;
+    }
+  }
+}
+
+}  // namespace
+
+void* level_kernel_ptr(bool shrec) {
+  return shrec ? reinterpret_cast<void*>(&cbp_level_kernel<true>)
+               : reinterpret_cast<void*>(&cbp_level_kernel<false>);
+}
+
+int level_max_threads() { return kLvlMaxThreads; }
+
+}  // namespace cbp

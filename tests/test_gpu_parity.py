@@ -503,7 +503,9 @@ def test_frame_parallel_kernel(monkeypatch, name, batch, ebn0, stop):
     qc = {"576": I.code_576, "2304": I.code_2304, "peg": I.code_peg_2048,
           "z4": lambda: I.relift(I.code_576(), 4), "z1": lambda: I.relift(I.code_576(), 1)}[name]()
     code = cbp.Code.from_qc(qc)
-    if name == "peg":
+    if name == "peg":  # the planner's choice is the wavefront kernel; without it, this one
+        assert code.launch_info(batch)["level_schedule"] == 1
+        monkeypatch.setenv("CBP_PLAN_LEVEL", "0")
         assert code.launch_info(batch)["frame_parallel"] == 1
         monkeypatch.setenv("CBP_PLAN_FP", "0")
         assert code.launch_info(batch)["frame_parallel"] == 0
@@ -517,6 +519,59 @@ def test_frame_parallel_kernel(monkeypatch, name, batch, ebn0, stop):
                                              threads=THREADS)
     assert_parity(run_gpu(code, fr.llr, "cbp_sp", max_iter=20, stop=stop), ref, f"{name} fp")
     assert (ref["iters"] > 0).any()
+
+
+LEVEL_CASES = [("peg", 700, 2.0, "syndrome", 64, "1"), ("peg", 129, 2.5, "none", 32, "0"),
+               ("peg", 300, 2.0, "syndrome", 96, "0"),
+               ("pegirr", 333, 1.75, "syndrome", 64, "0"), ("pegirr", 64, 1.5, "syndrome", 128, "1"),
+               ("z1", 500, 2.5, "syndrome", 64, "1"), ("z4", 300, 2.0, "syndrome", 96, "0"),
+               ("576", 257, 1.5, "syndrome", 64, "1"), ("2304", 100, 1.75, "syndrome", 64, "0")]
+
+
+@pytest.mark.parametrize("name,batch,ebn0,stop,lanes,shrec", LEVEL_CASES)
+def test_level_schedule_kernel(monkeypatch, name, batch, ebn0, stop, lanes, shrec):
+    # The checks of the expanded graph by level (a check's level is one more than that of
+    # the previous check of any of its variables), a level's checks on parallel lanes of one
+    # group per frame.  The planner picks it for the Z = 1 PEG codes; elsewhere it is forced
+    # on.  Lane groups of 32 to 128 lanes, levels wider and narrower than a group, edge
+    # records in shared or global memory, frames past a group's first, stop modes, soft
+    # output: bit for bit against the oracle.
+    qc = {"576": I.code_576, "2304": I.code_2304, "peg": I.code_peg_2048,
+          "pegirr": I.code_peg_irregular_2048,
+          "z4": lambda: I.relift(I.code_576(), 4), "z1": lambda: I.relift(I.code_576(), 1)}[name]()
+    code = cbp.Code.from_qc(qc)
+    if name.startswith("peg"):
+        info = code.launch_info(batch)
+        assert info["level_schedule"] == 1 and info["frame_parallel"] == 0
+    monkeypatch.setenv("CBP_PLAN_LEVEL", "1")
+    monkeypatch.setenv("CBP_LVL_LANES", str(lanes))
+    monkeypatch.setenv("CBP_LVL_SHREC", shrec)
+    info = code.launch_info(batch)
+    assert info["level_schedule"] == 1 and info["threads_per_cta"] % lanes == 0
+    fr = I.make_frames(qc, batch, ebn0, seed=4900 + batch, encoder="gf2" if qc.N <= 4096 else "tri")
+    ref = O.OracleCode(qc.base, qc.Z).decode(fr.llr, alg="cbp_sp", max_iter=20, stop=stop,
+                                             threads=THREADS)
+    assert_parity(run_gpu(code, fr.llr, "cbp_sp", max_iter=20, stop=stop), ref, f"{name} level")
+    if stop == "syndrome":
+        assert (ref["iters"] > 0).any()
+
+
+def test_level_schedule_host_decode_and_status(monkeypatch):
+    # the host-buffer entry point and the non-finite-LLR status through the same kernel
+    qc = I.code_peg_2048()
+    code = cbp.Code.from_qc(qc)
+    assert code.launch_info(700)["level_schedule"] == 1
+    fr = I.make_frames(qc, 700, 2.0, seed=4810)
+    host = torch.from_numpy(fr.llr).pin_memory()
+    h_ref, i_ref, _ = code.decode(host.cuda(), max_iter=20)
+    h, i = code.decode_host(host, max_iter=20, chunk=256)
+    assert torch.equal(i, i_ref.cpu()) and torch.equal(h, h_ref.cpu())
+    code.device_status()
+    bad = fr.llr.copy()
+    bad[5, 7] = np.nan
+    code.decode(torch.from_numpy(bad).cuda(), max_iter=5)
+    torch.cuda.synchronize()
+    assert code.device_status() == cbp.STATUS_NONFINITE_LLR
 
 
 def test_frame_parallel_kernel_on_the_26112_code(large, monkeypatch):
