@@ -10,8 +10,10 @@ static void* select_kernel(const Variant& v) {
       if (v.lvl) return level_kernel_ptr(v.shrec);
       return v.win ? sp_win_kernel_ptr(v.chk_shared)
                    : sp_kernel_ptr(v.chk_shared, v.fpt, v.wide, v.self_last);
-    case ALG_CBP_NMS:
-    case ALG_LBP_NMS: return minsum_kernel_ptr(v.alg, v.chk_shared, v.rstore);
+    case ALG_CBP_NMS: return minsum_kernel_ptr(v.alg, v.chk_shared, v.rstore);
+    case ALG_LBP_NMS:
+      if (v.lvl) return lbp_level_kernel_ptr(v.shrec);
+      return minsum_kernel_ptr(v.alg, v.chk_shared, v.rstore);
     case ALG_FBP_SP: return flood_kernel_ptr();
   }
   return nullptr;

@@ -211,7 +211,183 @@ __global__ void __launch_bounds__(kLvlMaxThreads, 1) cbp_level_kernel(const KPar
   }
 }
 
+// Layered normalized min-sum (Eqs. s2e10, s2e12), the comparator, on the same wavefront
+// schedule: a check reads and writes only its variables' Lambda and its own state, so the
+// levels order it exactly as the sequential schedule does.  Per group, shared memory
+// holds the check states (min1 | sgn, min2, position of min1, 32 sign bits) by
+// level-ordered check, Lambda for every variable and the decision bits; SHV instances
+// also copy each edge's variable index and the check offsets into shared memory.  The
+// arithmetic is the lane-parallel layered kernel's, operation for operation: pass 1 forms
+// Q = Lambda - R_old and the minima, pass 2 forms Q again from the same Lambda and R_old
+// (the same rounding) and Lambda = Q + R_new.
+constexpr int kLbpChunk = 4;
+constexpr float kLvlInf = __builtin_huge_valf();
+
+template <bool SHV>
+__global__ void __launch_bounds__(kLvlMaxThreads, 1) lbp_level_kernel(const KParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int G = p.lvl_lanes, F = p.F;
+  const int N = p.N, M = p.M, E = p.E, words = p.words;
+  const int tid = threadIdx.x;
+  const int g = tid / G, l = tid - g * G;
+  const float alpha = p.alpha;
+  unsigned char* sp = smem;
+  int* s_unsat = reinterpret_cast<int*>(sp);
+  sp += sizeof(int) * 16;
+  uint32_t* s_v = reinterpret_cast<uint32_t*>(sp);
+  int* s_e0 = reinterpret_cast<int*>(sp + sizeof(uint32_t) * ((E + 3) & ~3));
+  if (SHV) sp += sizeof(uint32_t) * ((E + 3) & ~3) + sizeof(int) * ((M + 1 + 3) & ~3);
+  if (tid < 16) s_unsat[tid] = 0;
+  if (SHV) {
+    for (int i = tid; i < E; i += blockDim.x) s_v[i] = p.lvl_edge[i].x & kSpMask;
+    for (int i = tid; i <= M; i += blockDim.x) s_e0[i] = p.lvl_e0[i];
+  }
+  __syncthreads();
+  if (g >= F) return;
+  const int* e0t = SHV ? s_e0 : p.lvl_e0;
+  const LvlEdge* __restrict__ led = p.lvl_edge;
+  float* gb = reinterpret_cast<float*>(sp) + static_cast<size_t>(g) * p.sh_frame;
+  uint4* AUX = reinterpret_cast<uint4*>(gb);
+  float* VAR = gb + 4 * static_cast<size_t>(M);
+  uint32_t* bits = reinterpret_cast<uint32_t*>(VAR + ((N + 3) & ~3));
+  const long long slot = static_cast<long long>(blockIdx.x) * F + g;
+  const int bar_id = 1 + g;
+  auto var_of = [&](int e) -> int {
+    return SHV ? static_cast<int>(s_v[e]) : static_cast<int>(__ldg(&led[e].x) & kSpMask);
+  };
+
+  for (long long frame = slot; frame < p.batch; frame += p.slots) {
+    const float* src = p.llr + frame * N;
+    bool bad = false;
+    for (int v = l; v < N; v += G) {  // Lambda_v = L_v (+0 turns -0 into +0)
+      const float L = __fadd_rn(__ldg(src + v), 0.0f);
+      bad |= non_finite(L);
+      VAR[v] = L;
+    }
+    if (bad) atomicOr(p.status, kStatusNonFiniteLlr);
+    team_sync(bar_id, G);
+
+    for (int t = 1;; ++t) {
+      for (int lv = 0; lv < p.nlev; ++lv) {
+        const int i1 = p.lvl_ptr[lv + 1];
+        for (int ci = p.lvl_ptr[lv] + l; ci < i1; ci += G) {
+          const int k0 = e0t[ci], d = e0t[ci + 1] - k0;
+          float r1 = 0.0f, r2 = 0.0f;
+          uint32_t osig = 0, oidx = 0, osg = 0;
+          if (t > 1) {  // rebuild R_old from the check's state of the previous sweep
+            const uint4 a = AUX[ci];
+            r1 = __fmul_rn(alpha, fabsf(__uint_as_float(a.x)));
+            r2 = __fmul_rn(alpha, __uint_as_float(a.y));
+            osig = a.x >> 31;
+            oidx = a.z;
+            osg = a.w;
+          }
+          float m1 = kLvlInf, m2 = kLvlInf;
+          uint32_t idx = 0, sig = 0, sg = 0;
+          for (int j0 = 0; j0 < d; j0 += kLbpChunk) {  // pass 1, Eq. (s2e10)
+            float lam[kLbpChunk];
+#pragma unroll
+            for (int u = 0; u < kLbpChunk; ++u)
+              if (j0 + u < d) lam[u] = VAR[var_of(k0 + j0 + u)];
+#pragma unroll
+            for (int u = 0; u < kLbpChunk; ++u) {
+              const int j = j0 + u;
+              if (j < d) {
+                float rold = 0.0f;
+                if (t > 1) {
+                  const float rm = (static_cast<uint32_t>(j) == oidx) ? r2 : r1;
+                  rold = (osig ^ ((osg >> j) & 1u)) ? -rm : rm;
+                }
+                const float q = __fsub_rn(lam[u], rold);
+                const float a = fabsf(q);
+                if (a < m1) {
+                  m2 = m1;
+                  m1 = a;
+                  idx = j;
+                } else if (a < m2) {
+                  m2 = a;
+                }
+                const uint32_t neg = q < 0.0f;
+                sig ^= neg;
+                sg |= neg << j;
+              }
+            }
+          }
+          const float n1 = __fmul_rn(alpha, m1), n2 = __fmul_rn(alpha, m2);
+          for (int j0 = 0; j0 < d; j0 += kLbpChunk) {  // pass 2, Eq. (s2e12)
+            float lam[kLbpChunk];
+            int vv[kLbpChunk];
+#pragma unroll
+            for (int u = 0; u < kLbpChunk; ++u)
+              if (j0 + u < d) {
+                vv[u] = var_of(k0 + j0 + u);
+                lam[u] = VAR[vv[u]];
+              }
+#pragma unroll
+            for (int u = 0; u < kLbpChunk; ++u) {
+              const int j = j0 + u;
+              if (j < d) {
+                float rold = 0.0f;
+                if (t > 1) {
+                  const float rm = (static_cast<uint32_t>(j) == oidx) ? r2 : r1;
+                  rold = (osig ^ ((osg >> j) & 1u)) ? -rm : rm;
+                }
+                const float q = __fsub_rn(lam[u], rold);
+                const float rm = (static_cast<uint32_t>(j) == idx) ? n2 : n1;
+                VAR[vv[u]] = __fadd_rn(q, (sig ^ ((sg >> j) & 1u)) ? -rm : rm);
+              }
+            }
+          }
+          AUX[ci] = make_uint4(__float_as_uint(sig ? -m1 : m1), __float_as_uint(m2), idx, sg);
+        }
+        team_sync(bar_id, G);
+      }
+      // ---- decisions (Eq. s2e7) on Lambda, packed by warp ballot; syndrome
+      for (int vb = 0; vb < N; vb += G) {
+        const int v = vb + l;
+        bool neg = false;
+        if (v < N) {
+          const float lb = VAR[v];
+          neg = lb < 0.0f;
+          if (p.soft) p.soft[frame * N + v] = lb;
+        }
+        const unsigned wv = __ballot_sync(0xffffffffu, neg);
+        if ((l & 31) == 0 && v < N) bits[v >> 5] = wv;
+      }
+      team_sync(bar_id, G);
+      bool fail = false;
+      for (int ci = l; ci < M; ci += G) {
+        uint32_t par = 0;
+        const int e1 = e0t[ci + 1];
+        for (int e = e0t[ci]; e < e1; ++e) {
+          const uint32_t v = static_cast<uint32_t>(var_of(e));
+          par ^= bits[v >> 5] >> (v & 31);
+        }
+        fail |= (par & 1u) != 0;
+      }
+      if (fail) s_unsat[g] = 1;
+      team_sync(bar_id, G);
+      const bool ok = *static_cast<volatile int*>(&s_unsat[g]) == 0;
+      const bool done = (ok && p.stop == CBP_STOP_SYNDROME) || t >= p.max_iter;
+      if (done) {
+        uint32_t* ho = p.hard + frame * words;
+        for (int w = l; w < words; w += G) ho[w] = bits[w];
+        if (l == 0) p.iters[frame] = ok ? t : -t;
+      }
+      team_sync(bar_id, G);
+      if (l == 0) s_unsat[g] = 0;
+      team_sync(bar_id, G);
+      if (done) break;
+    }
+  }
+}
+
 }  // namespace
+
+void* lbp_level_kernel_ptr(bool shv) {
+  return shv ? reinterpret_cast<void*>(&lbp_level_kernel<true>)
+             : reinterpret_cast<void*>(&lbp_level_kernel<false>);
+}
 
 void* level_kernel_ptr(bool shrec) {
   return shrec ? reinterpret_cast<void*>(&cbp_level_kernel<true>)
