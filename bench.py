@@ -55,20 +55,20 @@ OPS_SYN = 1
 # the numbers are stale and the bench line reports null instead.
 CAPTURES = {
     "cbp_sp": {"kernel": "cbp_sp_kernel<0, 1, 3, 0, 768, 1>(KParams)", "date": "2026-12-04", "frames": 2432,
-               "sources": "dc04346ffe27882a", "dram_bytes_per_frame_sweep": 1392031,
-               "thread_inst_per_edge_sweep": 92.1, "issue_active": 0.523,
+               "sources": "4e097cb25fec23a2", "dram_bytes_per_frame_sweep": 1392736,
+               "thread_inst_per_edge_sweep": 92.1, "issue_active": 0.527,
                "warps_active_per_sm": 23.9},
     "lbp_nms": {"kernel": "minsum_kernel<2, 0, 768, 0>(KParams)", "date": "2026-12-04", "frames": 2432,
-               "sources": "1ce95475ae5758a6", "dram_bytes_per_frame_sweep": 506329,
-               "thread_inst_per_edge_sweep": 73.1, "issue_active": 0.573,
+               "sources": "1272777b564edc2b", "dram_bytes_per_frame_sweep": 502817,
+               "thread_inst_per_edge_sweep": 73.1, "issue_active": 0.579,
                "warps_active_per_sm": 22.6},
     "cbp_nms": {"kernel": "minsum_kernel<1, 0, 768, 0>(KParams)", "date": "2026-12-04", "frames": 2432,
-               "sources": "1ce95475ae5758a6", "dram_bytes_per_frame_sweep": 848588,
-               "thread_inst_per_edge_sweep": 92.8, "issue_active": 0.578,
-               "warps_active_per_sm": 22.2},
+               "sources": "1272777b564edc2b", "dram_bytes_per_frame_sweep": 845818,
+               "thread_inst_per_edge_sweep": 92.8, "issue_active": 0.583,
+               "warps_active_per_sm": 22.1},
     "fbp_sp": {"kernel": "flood_kernel(KParams)", "date": "2026-12-04", "frames": 2432,
-               "sources": "60e20b4e44759bec", "dram_bytes_per_frame_sweep": 788498,
-               "thread_inst_per_edge_sweep": 109.7, "issue_active": 0.32,
+               "sources": "e936733ed0262d4c", "dram_bytes_per_frame_sweep": 790972,
+               "thread_inst_per_edge_sweep": 109.7, "issue_active": 0.324,
                "warps_active_per_sm": 12.0},
 }
 
