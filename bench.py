@@ -542,7 +542,10 @@ def run_learned(args):
         ev[0].record(stream)
         # checkpoint spacing T: the forward records the tape, the backward recomputes nothing
         soft = cbp.weighted_cbp(code, llr, w, T, T)
-        loss = torch.nn.functional.binary_cross_entropy_with_logits(-soft, cw.float())
+        if args.loss == "bce":
+            loss = torch.nn.functional.binary_cross_entropy_with_logits(-soft, cw.float())
+        else:  # soft bit-error rate: mean sigmoid of the margin by which a bit is wrong
+            loss = torch.sigmoid(soft * (2.0 * cw.float() - 1.0)).mean()
         opt.zero_grad(set_to_none=True)
         ev[1].record(stream)
         loss.backward()
@@ -598,7 +601,8 @@ def run_learned(args):
             print(json.dumps(row), flush=True)
     print(json.dumps({"code": args.learned_code, "zero_codeword": zero,
                       "learned_weights": wl.cpu().numpy().round(4).tolist(),
-                      "train_steps": args.train_steps, "train_frames": B,
+                      "train_steps": args.train_steps, "train_frames": B, "loss": args.loss,
+                      "lr": args.lr,
                       "train_seconds": train_s, "train_step_ms_median": step_ms,
                       "loss_first_last": [losses[0], losses[-1]]}),
           flush=True)
@@ -821,6 +825,9 @@ def main():
     ap.add_argument("--train-frames", type=int, default=8192)
     ap.add_argument("--eval-frames", type=int, default=1_000_000)
     ap.add_argument("--lr", type=float, default=0.01)
+    ap.add_argument("--loss", default="bce", choices=["bce", "soft_ber"],
+                    help="learned weights: mean BCE of the output LLRs, or the mean sigmoid of "
+                         "each bit's wrong-side margin (a smooth bit-error rate)")
     ap.add_argument("--sweep-lo", type=float, default=0.0)
     ap.add_argument("--sweep-hi", type=float, default=2.0)
     ap.add_argument("--no-comparators", action="store_true")
