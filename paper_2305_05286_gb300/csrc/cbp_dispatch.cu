@@ -10,7 +10,9 @@ static void* select_kernel(const Variant& v) {
       if (v.lvl) return level_kernel_ptr(v.shrec);
       return v.win ? sp_win_kernel_ptr(v.chk_shared)
                    : sp_kernel_ptr(v.chk_shared, v.fpt, v.wide, v.self_last);
-    case ALG_CBP_NMS: return minsum_kernel_ptr(v.alg, v.chk_shared, v.rstore);
+    case ALG_CBP_NMS:
+      if (v.lvl) return nms_level_kernel_ptr(v.shrec);
+      return minsum_kernel_ptr(v.alg, v.chk_shared, v.rstore);
     case ALG_LBP_NMS:
       if (v.lvl) return lbp_level_kernel_ptr(v.shrec);
       return minsum_kernel_ptr(v.alg, v.chk_shared, v.rstore);

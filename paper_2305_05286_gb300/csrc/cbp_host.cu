@@ -116,6 +116,8 @@ int device_init(int dev, DeviceInfo** out) {
                            {ALG_CBP_SP, false, 1, false, false, false, false, false, true, true},
                            {ALG_LBP_NMS, false, 1, false, false, false, false, false, true},
                            {ALG_LBP_NMS, false, 1, false, false, false, false, false, true, true},
+                           {ALG_CBP_NMS, false, 1, false, false, false, false, false, true},
+                           {ALG_CBP_NMS, false, 1, false, false, false, false, false, true, true},
                            {ALG_CBP_NMS, true, 1}, {ALG_CBP_NMS, false, 1},
                            {ALG_CBP_NMS, true, 1, false, false, false, false, true},
                            {ALG_CBP_NMS, false, 1, false, false, false, false, true},
@@ -342,19 +344,21 @@ int make_fp_plan(const cbp_code* c, const DeviceInfo& di, int batch, Plan* out) 
 // holds each group slot's C2V messages.  The edge records go to shared memory too when
 // the code has the 8-byte form and a frame still fits (CBP_LVL_SHREC=0 keeps them in
 // global memory).  Layered NMS (alg ALG_LBP_NMS): per frame Lambda and the check states
-// instead, no phi table, no workspace, each edge's variable index in shared memory.
+// instead, no phi table, no workspace, each edge's variable index in shared memory.  CBP
+// min-sum (ALG_CBP_NMS): per frame Q* and (min1 | sgn, min2) per check, no phi table.
 int make_level_plan(const cbp_code* c, const DeviceInfo& di, int batch, Plan* out,
                     int alg = ALG_CBP_SP) {
   if (c->nlev == 0) return CBP_EUNSUPPORTED;
-  const bool lbp = alg == ALG_LBP_NMS;
+  const bool lbp = alg == ALG_LBP_NMS, nms = alg == ALG_CBP_NMS;
   if (lbp && c->maxdeg > kMaxDeg) return CBP_EUNSUPPORTED;
   Plan pl;
   pl.v = Variant{alg, false, 1};
   pl.v.lvl = true;
-  size_t fixed = (lbp ? 0 : sizeof(float4) * kPhiSegments) + sizeof(int) * 16;
+  size_t fixed = (lbp || nms ? 0 : sizeof(float4) * kPhiSegments) + sizeof(int) * 16;
   const size_t W = align4((static_cast<size_t>(c->N) + 31) / 32);
-  const size_t fr_floats = lbp ? 4 * static_cast<size_t>(c->M) + align4(c->N) + W
-                               : 2 * static_cast<size_t>(c->N) + align4(c->M) + W;
+  const size_t fr_floats = lbp   ? 4 * static_cast<size_t>(c->M) + align4(c->N) + W
+                           : nms ? 2 * static_cast<size_t>(c->M) + align4(c->N) + W
+                                 : 2 * static_cast<size_t>(c->N) + align4(c->M) + W;
   const size_t avail = static_cast<size_t>(di.smem_optin);
   const size_t recb = (lbp ? sizeof(uint32_t) * align4(c->E) : sizeof(uint2) * c->E) +
                       sizeof(int) * align4(c->M + 1);
@@ -522,7 +526,8 @@ int make_lane_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, 
 // CBP_PLAN_FP=0 keeps the lane-parallel plan, CBP_PLAN_LEVEL=0 skips the wavefront kernel.
 int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan* out,
               int stop = CBP_STOP_SYNDROME, bool allow_fp = true) {
-  if (alg == ALG_LBP_NMS && allow_fp) {  // layered NMS: the same choice, no frame-parallel kernel
+  if ((alg == ALG_LBP_NMS || alg == ALG_CBP_NMS) && allow_fp) {  // the same choice, no
+                                                                // frame-parallel kernel
     const char* el = std::getenv("CBP_PLAN_LEVEL");
     if (el && el[0] == '1') return make_level_plan(c, di, batch, out, alg);
     const int rc = make_lane_plan(c, di, alg, batch, out, stop);

@@ -203,7 +203,7 @@ struct Variant {
   bool self_last = false;  // CBP-SP, one frame per group: every weight-1 edge ends its row
   bool fp = false;         // CBP-SP, frame-parallel kernel: one frame per thread
   bool rstore = false;     // CBP min-sum: C2V messages kept per edge (no rebuild)
-  bool lvl = false;        // CBP-SP / layered NMS on the wavefront schedule of the expanded graph
+  bool lvl = false;        // CBP-SP / min-sum on the wavefront schedule of the expanded graph
   bool shrec = false;      // that kernel with its edge records in shared memory
 };
 
@@ -228,6 +228,7 @@ cudaError_t decoder_occupancy(const Variant& v, int threads, size_t smem, int* c
 void* sp_kernel_ptr(bool chk_shared, int fpt, bool wide, bool self_last);  // cbp_sp.cu
 void* level_kernel_ptr(bool shrec);  // cbp_level.cu
 void* lbp_level_kernel_ptr(bool shv);
+void* nms_level_kernel_ptr(bool shrec);
 int level_max_threads();
 void* sp_multi_kernel_ptr(bool chk_shared, int fpt, bool self_last);  // cbp_sp.cu
 void* sp_win_kernel_ptr(bool chk_shared);                   // cbp_sp.cu

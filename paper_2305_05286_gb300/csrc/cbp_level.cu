@@ -382,7 +382,164 @@ __global__ void __launch_bounds__(kLvlMaxThreads, 1) lbp_level_kernel(const KPar
   }
 }
 
+// CBP normalized min-sum (Eqs. s4e18xx, s4e21xx) on the same schedule and tables: the
+// log-tanh kernel's structure with the check state (min1 | sgn Omega, min2) in place of
+// the check-belief and Q* alone per variable; the C2V messages per edge in the workspace
+// (B2V writes the predecessor's slot, V2C reads the edge's own slot).  The arithmetic is
+// the lane-parallel CBP min-sum kernel's with per-edge messages, operation for operation.
+template <bool SHREC>
+__global__ void __launch_bounds__(kLvlMaxThreads, 1) nms_level_kernel(const KParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int G = p.lvl_lanes, F = p.F;
+  const int N = p.N, M = p.M, E = p.E, words = p.words;
+  const int tid = threadIdx.x;
+  const int g = tid / G, l = tid - g * G;
+  const float alpha = p.alpha;
+  unsigned char* sp = smem;
+  int* s_unsat = reinterpret_cast<int*>(sp);
+  sp += sizeof(int) * 16;
+  uint2* s_rec = reinterpret_cast<uint2*>(sp);
+  int* s_e0 = reinterpret_cast<int*>(sp + sizeof(uint2) * E);
+  if (SHREC) sp += sizeof(uint2) * E + sizeof(int) * ((M + 1 + 3) & ~3);
+  if (tid < 16) s_unsat[tid] = 0;
+  if (SHREC) {
+    for (int i = tid; i < E; i += blockDim.x) s_rec[i] = p.lvl_rec8[i];
+    for (int i = tid; i <= M; i += blockDim.x) s_e0[i] = p.lvl_e0[i];
+  }
+  __syncthreads();
+  if (g >= F) return;
+  const int* e0t = SHREC ? s_e0 : p.lvl_e0;
+  const LvlEdge* __restrict__ led = p.lvl_edge;
+  float* gb = reinterpret_cast<float*>(sp) + static_cast<size_t>(g) * p.sh_frame;
+  float2* CHK = reinterpret_cast<float2*>(gb);
+  float* Q = gb + 2 * static_cast<size_t>(M);
+  uint32_t* bits = reinterpret_cast<uint32_t*>(Q + ((N + 3) & ~3));
+  const long long slot = static_cast<long long>(blockIdx.x) * F + g;
+  float* R = p.ws + slot * p.ws_slot;
+  const int bar_id = 1 + g;
+
+  for (long long frame = slot; frame < p.batch; frame += p.slots) {
+    const float* src = p.llr + frame * N;
+    bool bad = false;
+    for (int v = l; v < N; v += G) {  // Q*_v = L_v (+0 turns -0 into +0)
+      const float L = __fadd_rn(__ldg(src + v), 0.0f);
+      bad |= non_finite(L);
+      Q[v] = L;
+    }
+    if (bad) atomicOr(p.status, kStatusNonFiniteLlr);
+    team_sync(bar_id, G);
+
+    for (int t = 1;; ++t) {
+      for (int lv = 0; lv < p.nlev; ++lv) {
+        const int i1 = p.lvl_ptr[lv + 1];
+        for (int ci = p.lvl_ptr[lv] + l; ci < i1; ci += G) {
+          const int e0 = e0t[ci], e1 = e0t[ci + 1];
+          float m1 = kLvlInf, m2 = kLvlInf;
+          uint32_t sig = 0;
+          for (int eb = e0; eb < e1; eb += kLbpChunk) {
+            float q[kLbpChunk], ro[kLbpChunk];
+            float2 pc[kLbpChunk];
+            uint32_t vx[kLbpChunk];
+            int pe[kLbpChunk];
+#pragma unroll
+            for (int u = 0; u < kLbpChunk; ++u) {  // loads of the chunk
+              const int e = eb + u;
+              if (e < e1) {
+                const LvlRec rec = lvl_rec<SHREC>(s_rec, led, e);
+                vx[u] = rec.vx;
+                pe[u] = rec.pe;
+                q[u] = Q[rec.vx & kSpMask];
+                pc[u] = CHK[rec.cj];
+                ro[u] = (t > 1 && !(rec.vx & kSpSelf)) ? R[e] : 0.0f;
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < kLbpChunk; ++u) {
+              const int e = eb + u;
+              if (e < e1) {
+                const bool self = vx[u] & kSpSelf;
+                const bool first = (t == 1) && (vx[u] & kSpFirst);
+                // B2V, Eq. (s4e18xx): min2 of c_j when |Q*_v| is its min1
+                float Rn = 0.0f;
+                if (!first) {
+                  const float b1 = fabsf(pc[u].x);
+                  const float rm = __fmul_rn(alpha, (fabsf(q[u]) == b1) ? pc[u].y : b1);
+                  Rn = (sign_bit(pc[u].x) ^ (q[u] < 0.0f)) ? -rm : rm;
+                }
+                float rold;
+                if (self) {
+                  rold = Rn;  // c_j == c_i
+                } else {
+                  rold = ro[u];
+                  if (!first) R[pe[u]] = Rn;  // Eq. (s4e22)
+                }
+                const float qn = __fsub_rn(__fadd_rn(q[u], Rn), rold);  // Eq. (s4e19)
+                const float a = fabsf(qn);                                 // C2B, Eq. (s4e21xx)
+                if (a < m1) {
+                  m2 = m1;
+                  m1 = a;
+                } else if (a < m2) {
+                  m2 = a;
+                }
+                sig ^= qn < 0.0f;
+                Q[vx[u] & kSpMask] = qn;
+              }
+            }
+          }
+          CHK[ci] = make_float2(sig ? -m1 : m1, m2);
+        }
+        team_sync(bar_id, G);
+      }
+      // ---- flushed posterior (Eq. s4e20 with the last check of v as c_j), decisions
+      for (int vb = 0; vb < N; vb += G) {
+        const int v = vb + l;
+        bool neg = false;
+        if (v < N) {
+          const float q = Q[v];
+          const float2 pc = CHK[__ldg(p.last_chk + v)];
+          const float b1 = fabsf(pc.x);
+          const float rm = __fmul_rn(alpha, (fabsf(q) == b1) ? pc.y : b1);
+          const float lb = __fadd_rn(q, (sign_bit(pc.x) ^ (q < 0.0f)) ? -rm : rm);
+          neg = lb < 0.0f;
+          if (p.soft) p.soft[frame * N + v] = lb;
+        }
+        const unsigned wv = __ballot_sync(0xffffffffu, neg);
+        if ((l & 31) == 0 && v < N) bits[v >> 5] = wv;
+      }
+      team_sync(bar_id, G);
+      bool fail = false;
+      for (int ci = l; ci < M; ci += G) {
+        uint32_t par = 0;
+        const int e1 = e0t[ci + 1];
+        for (int e = e0t[ci]; e < e1; ++e) {
+          const uint32_t v = lvl_rec<SHREC>(s_rec, led, e).vx & kSpMask;
+          par ^= bits[v >> 5] >> (v & 31);
+        }
+        fail |= (par & 1u) != 0;
+      }
+      if (fail) s_unsat[g] = 1;
+      team_sync(bar_id, G);
+      const bool ok = *static_cast<volatile int*>(&s_unsat[g]) == 0;
+      const bool done = (ok && p.stop == CBP_STOP_SYNDROME) || t >= p.max_iter;
+      if (done) {
+        uint32_t* ho = p.hard + frame * words;
+        for (int w = l; w < words; w += G) ho[w] = bits[w];
+        if (l == 0) p.iters[frame] = ok ? t : -t;
+      }
+      team_sync(bar_id, G);
+      if (l == 0) s_unsat[g] = 0;
+      team_sync(bar_id, G);
+      if (done) break;
+    }
+  }
+}
+
 }  // namespace
+
+void* nms_level_kernel_ptr(bool shrec) {
+  return shrec ? reinterpret_cast<void*>(&nms_level_kernel<true>)
+               : reinterpret_cast<void*>(&nms_level_kernel<false>);
+}
 
 void* lbp_level_kernel_ptr(bool shv) {
   return shv ? reinterpret_cast<void*>(&lbp_level_kernel<true>)

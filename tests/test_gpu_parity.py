@@ -562,26 +562,27 @@ LBP_LEVEL_CASES = [("peg", 700, 2.0, 0.75, 96, "1"), ("peg", 300, 1.75, 1.0, 64,
                    ("2304", 100, 2.0, 1.0, 64, "1")]
 
 
+@pytest.mark.parametrize("alg", ["lbp_nms", "cbp_nms"])
 @pytest.mark.parametrize("name,batch,ebn0,alpha,lanes,shv", LBP_LEVEL_CASES)
-def test_level_schedule_layered_min_sum(monkeypatch, name, batch, ebn0, alpha, lanes, shv):
-    # The layered min-sum comparator on the same wavefront schedule: the planner's choice for
-    # the Z = 1 PEG codes, forced elsewhere; normalisations, lane groups, variable indices
-    # in shared or global memory, soft output (Lambda): bit for bit against the oracle.
+def test_level_schedule_min_sum(monkeypatch, alg, name, batch, ebn0, alpha, lanes, shv):
+    # Layered min-sum and CBP min-sum on the same wavefront schedule: the planner's choice for
+    # the Z = 1 PEG codes, forced elsewhere; normalisations, lane groups, edge records in
+    # shared or global memory, soft output: bit for bit against the oracle.
     qc = {"576": I.code_576, "2304": I.code_2304, "peg": I.code_peg_2048,
           "pegirr": I.code_peg_irregular_2048,
           "z4": lambda: I.relift(I.code_576(), 4)}[name]()
     code = cbp.Code.from_qc(qc)
     if name.startswith("peg"):
-        assert code.launch_info(batch, alg="lbp_nms")["level_schedule"] == 1
+        assert code.launch_info(batch, alg=alg)["level_schedule"] == 1
     monkeypatch.setenv("CBP_PLAN_LEVEL", "1")
     monkeypatch.setenv("CBP_LVL_LANES", str(lanes))
     monkeypatch.setenv("CBP_LVL_SHREC", shv)
-    assert code.launch_info(batch, alg="lbp_nms")["level_schedule"] == 1
+    assert code.launch_info(batch, alg=alg)["level_schedule"] == 1
     fr = I.make_frames(qc, batch, ebn0, seed=5100 + batch)
-    ref = O.OracleCode(qc.base, qc.Z).decode(fr.llr, alg="lbp_nms", max_iter=20, alpha=alpha,
+    ref = O.OracleCode(qc.base, qc.Z).decode(fr.llr, alg=alg, max_iter=20, alpha=alpha,
                                              threads=THREADS)
-    got = run_gpu(code, fr.llr, "lbp_nms", max_iter=20, alpha=alpha)
-    assert_parity(got, ref, f"{name} layered level")
+    got = run_gpu(code, fr.llr, alg, max_iter=20, alpha=alpha)
+    assert_parity(got, ref, f"{name} {alg} level")
     assert (ref["iters"] > 0).any()
 
 
