@@ -236,6 +236,7 @@ struct cbp_code {
   bool self_last = true;     // every row holds at most one weight-1 entry, as its last
   int nlev = 0;              // levels of the wavefront schedule (0: tables not built)
   int lvl_maxw = 0;          // checks in its widest level
+  int lvl_test = 0;          // that level
   CodeDev d;
   Shape shape() const {
     return Shape{Z, N, M, E, nnzb, mb, nb, (N + 31) / 32, ncomp, nself};
@@ -609,6 +610,7 @@ KParams code_params(const cbp_code* c, const DeviceInfo& di, const Plan& pl, int
   p.last_chk = c->d.last_chk;
   p.nlev = c->nlev;
   p.lvl_lanes = pl.lvl_lanes;
+  p.lvl_test = c->lvl_test;
   return p;
 }
 
@@ -672,7 +674,11 @@ int build_level_tables(cbp_code* c, const std::vector<BaseEdge>& edges,
   }
   std::vector<int> lptr(nlev + 1, 0), order(M), newidx(E);
   for (int m = 0; m < M; ++m) ++lptr[level[m] + 1];
-  for (int l = 0; l < nlev; ++l) c->lvl_maxw = std::max(c->lvl_maxw, lptr[l + 1]);
+  for (int l = 0; l < nlev; ++l)
+    if (lptr[l + 1] > c->lvl_maxw) {
+      c->lvl_maxw = lptr[l + 1];
+      c->lvl_test = l;
+    }
   for (int l = 0; l < nlev; ++l) lptr[l + 1] += lptr[l];
   {
     std::vector<int> fill(lptr.begin(), lptr.end() - 1);

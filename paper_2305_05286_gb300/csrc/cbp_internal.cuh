@@ -172,6 +172,7 @@ struct KParams {
   const uint2* lvl_rec8;
   const int* last_chk;
   int nlev, lvl_lanes;
+  int lvl_test;           // the widest level (tested first at a sweep's end)
 };
 
 // Several codes in one launch (CBP-SP): per-code parameters and the chunk list.

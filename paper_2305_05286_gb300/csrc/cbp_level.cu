@@ -162,6 +162,36 @@ __global__ void __launch_bounds__(kLvlMaxThreads, 1) cbp_level_kernel(const KPar
         }
         team_sync(bar_id, G);
       }
+      // ---- sweep-end test: a frame stops only when every check holds, so the checks of
+      // the widest level are evaluated first (on the read-only flushed posterior); when one
+      // fails, the full flush and syndrome are skipped (the same decision)
+      bool full = t >= p.max_iter;
+      if (!full && p.stop == CBP_STOP_SYNDROME) {
+        bool fail = false;
+        const int j1 = p.lvl_ptr[p.lvl_test + 1];
+        for (int ci = p.lvl_ptr[p.lvl_test] + l; ci < j1; ci += G) {
+          uint32_t par = 0;
+          const int e1 = e0t[ci + 1];
+          for (int e = e0t[ci]; e < e1; ++e) {
+            const int v = static_cast<int>(lvl_rec<SHREC>(s_rec, led, e).vx & kSpMask);
+            const float2 qp = QP[v];
+            const float Sk = S[__ldg(p.last_chk + v)];
+            const float mag = phi_eval(fabsf(__fsub_rn(fabsf(Sk), qp.y)), xlo, tab);
+            const float lb = __fadd_rn(
+                qp.x, __uint_as_float(__float_as_uint(mag) |
+                                      ((__float_as_uint(Sk) ^ __float_as_uint(qp.x)) &
+                                       0x80000000u)));
+            par ^= lb < 0.0f ? 1u : 0u;
+          }
+          fail |= (par & 1u) != 0;
+        }
+        if (fail) s_unsat[g] = 1;
+        team_sync(bar_id, G);
+        full = *static_cast<volatile int*>(&s_unsat[g]) == 0;
+        team_sync(bar_id, G);
+        if (l == 0) s_unsat[g] = 0;
+      }
+      if (!full) continue;
       // ---- flushed posterior (Eq. s4e20 with the last check of v, read-only) and the
       // decisions (Eq. s2e7): lane l takes v = l, l + G, ...; a warp's 32 variables of one
       // step are one aligned word
@@ -342,6 +372,30 @@ __global__ void __launch_bounds__(kLvlMaxThreads, 1) lbp_level_kernel(const KPar
         }
         team_sync(bar_id, G);
       }
+      // ---- sweep-end test: a frame stops only when every check holds, so the checks of
+      // the widest level are evaluated first (on the read-only flushed posterior); when one
+      // fails, the full flush and syndrome are skipped (the same decision)
+      bool full = t >= p.max_iter;
+      if (!full && p.stop == CBP_STOP_SYNDROME) {
+        bool fail = false;
+        const int j1 = p.lvl_ptr[p.lvl_test + 1];
+        for (int ci = p.lvl_ptr[p.lvl_test] + l; ci < j1; ci += G) {
+          uint32_t par = 0;
+          const int e1 = e0t[ci + 1];
+          for (int e = e0t[ci]; e < e1; ++e) {
+            const int v = var_of(e);
+            const float lb = VAR[v];
+            par ^= lb < 0.0f ? 1u : 0u;
+          }
+          fail |= (par & 1u) != 0;
+        }
+        if (fail) s_unsat[g] = 1;
+        team_sync(bar_id, G);
+        full = *static_cast<volatile int*>(&s_unsat[g]) == 0;
+        team_sync(bar_id, G);
+        if (l == 0) s_unsat[g] = 0;
+      }
+      if (!full) continue;
       // ---- decisions (Eq. s2e7) on Lambda, packed by warp ballot; syndrome
       for (int vb = 0; vb < N; vb += G) {
         const int v = vb + l;
@@ -490,6 +544,34 @@ __global__ void __launch_bounds__(kLvlMaxThreads, 1) nms_level_kernel(const KPar
         }
         team_sync(bar_id, G);
       }
+      // ---- sweep-end test: a frame stops only when every check holds, so the checks of
+      // the widest level are evaluated first (on the read-only flushed posterior); when one
+      // fails, the full flush and syndrome are skipped (the same decision)
+      bool full = t >= p.max_iter;
+      if (!full && p.stop == CBP_STOP_SYNDROME) {
+        bool fail = false;
+        const int j1 = p.lvl_ptr[p.lvl_test + 1];
+        for (int ci = p.lvl_ptr[p.lvl_test] + l; ci < j1; ci += G) {
+          uint32_t par = 0;
+          const int e1 = e0t[ci + 1];
+          for (int e = e0t[ci]; e < e1; ++e) {
+            const int v = static_cast<int>(lvl_rec<SHREC>(s_rec, led, e).vx & kSpMask);
+            const float q = Q[v];
+            const float2 pc = CHK[__ldg(p.last_chk + v)];
+            const float b1 = fabsf(pc.x);
+            const float rm = __fmul_rn(alpha, (fabsf(q) == b1) ? pc.y : b1);
+            const float lb = __fadd_rn(q, (sign_bit(pc.x) ^ (q < 0.0f)) ? -rm : rm);
+            par ^= lb < 0.0f ? 1u : 0u;
+          }
+          fail |= (par & 1u) != 0;
+        }
+        if (fail) s_unsat[g] = 1;
+        team_sync(bar_id, G);
+        full = *static_cast<volatile int*>(&s_unsat[g]) == 0;
+        team_sync(bar_id, G);
+        if (l == 0) s_unsat[g] = 0;
+      }
+      if (!full) continue;
       // ---- flushed posterior (Eq. s4e20 with the last check of v as c_j), decisions
       for (int vb = 0; vb < N; vb += G) {
         const int v = vb + l;
