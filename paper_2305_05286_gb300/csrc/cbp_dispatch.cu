@@ -16,7 +16,7 @@ static void* select_kernel(const Variant& v) {
     case ALG_LBP_NMS:
       if (v.lvl) return lbp_level_kernel_ptr(v.shrec);
       return minsum_kernel_ptr(v.alg, v.chk_shared, v.rstore);
-    case ALG_FBP_SP: return flood_kernel_ptr();
+    case ALG_FBP_SP: return v.lvl ? fbp_level_kernel_ptr(v.shrec, v.deg) : flood_kernel_ptr();
   }
   return nullptr;
 }

@@ -124,6 +124,14 @@ int device_init(int dev, DeviceInfo** out) {
                            {ALG_LBP_NMS, false, 1}, {ALG_FBP_SP, false, 1}};
     for (const Variant& v : all)
       if (decoder_set_smem(v, d.smem_optin) != cudaSuccess) return CBP_ECUDA;
+    for (int deg : {8, 16, kMaxDeg})  // the wavefront flooding kernel's degree buckets
+      for (bool sh : {false, true}) {
+        Variant v{ALG_FBP_SP, false, 1};
+        v.lvl = true;
+        v.shrec = sh;
+        v.deg = deg;
+        if (decoder_set_smem(v, d.smem_optin) != cudaSuccess) return CBP_ECUDA;
+      }
     if (grad_set_smem(d.smem_optin) != cudaSuccess) return CBP_ECUDA;
     for (int chk = 0; chk < 2; ++chk)
       for (int fpt = 1; fpt <= 3; ++fpt) {  // 3: one frame per group, weight-1-last instance
@@ -347,11 +355,12 @@ int make_fp_plan(const cbp_code* c, const DeviceInfo& di, int batch, Plan* out) 
 // global memory).  Layered NMS (alg ALG_LBP_NMS): per frame Lambda and the check states
 // instead, no phi table, no workspace, each edge's variable index in shared memory.  CBP
 // min-sum (ALG_CBP_NMS): per frame Q* and (min1 | sgn, min2) per check, no phi table.
+// Flooding (ALG_FBP_SP): per frame Lambda; the variables' edge lists in shared memory too.
 int make_level_plan(const cbp_code* c, const DeviceInfo& di, int batch, Plan* out,
                     int alg = ALG_CBP_SP) {
   if (c->nlev == 0) return CBP_EUNSUPPORTED;
-  const bool lbp = alg == ALG_LBP_NMS, nms = alg == ALG_CBP_NMS;
-  if (lbp && c->maxdeg > kMaxDeg) return CBP_EUNSUPPORTED;
+  const bool lbp = alg == ALG_LBP_NMS, nms = alg == ALG_CBP_NMS, fbp = alg == ALG_FBP_SP;
+  if ((lbp || fbp) && c->maxdeg > kMaxDeg) return CBP_EUNSUPPORTED;
   Plan pl;
   pl.v = Variant{alg, false, 1};
   pl.v.lvl = true;
@@ -359,19 +368,25 @@ int make_level_plan(const cbp_code* c, const DeviceInfo& di, int batch, Plan* ou
   const size_t W = align4((static_cast<size_t>(c->N) + 31) / 32);
   const size_t fr_floats = lbp   ? 4 * static_cast<size_t>(c->M) + align4(c->N) + W
                            : nms ? 2 * static_cast<size_t>(c->M) + align4(c->N) + W
+                           : fbp ? align4(c->N) + W
                                  : 2 * static_cast<size_t>(c->N) + align4(c->M) + W;
   const size_t avail = static_cast<size_t>(di.smem_optin);
-  const size_t recb = (lbp ? sizeof(uint32_t) * align4(c->E) : sizeof(uint2) * c->E) +
-                      sizeof(int) * align4(c->M + 1);
+  const size_t recb = fbp ? sizeof(int) * (2 * align4(c->E) + align4(c->M + 1) + align4(c->N + 1))
+                          : (lbp ? sizeof(uint32_t) * align4(c->E) : sizeof(uint2) * c->E) +
+                                sizeof(int) * align4(c->M + 1);
+  if (fbp) pl.v.deg = c->maxdeg <= 8 ? 8 : c->maxdeg <= 16 ? 16 : kMaxDeg;
   const char* es = std::getenv("CBP_LVL_SHREC");
-  if ((lbp || c->d.lvl_rec8) && !(es && es[0] == '0') && fixed + recb + fr_floats * 4 <= avail) {
+  if ((lbp || fbp || c->d.lvl_rec8) && !(es && es[0] == '0') &&
+      fixed + recb + fr_floats * 4 <= avail) {
     pl.v.shrec = true;
     fixed += recb;
   }
   if (fixed + fr_floats * 4 > avail) return CBP_EUNSUPPORTED;
   int F = static_cast<int>(std::min<size_t>((avail - fixed) / (fr_floats * 4), 15));
-  int G = std::max(32, std::min((level_max_threads() / F) / 32 * 32,
-                                (c->lvl_maxw + 31) / 32 * 32));
+  // (flooding takes all checks at once, so the level widths do not bound its groups)
+  int G = fbp ? 64
+              : std::max(32, std::min((level_max_threads() / F) / 32 * 32,
+                                      (c->lvl_maxw + 31) / 32 * 32));
   if (const char* e = std::getenv("CBP_LVL_LANES")) {
     const int g = std::atoi(e);
     if (g >= 32 && g <= 256 && g % 32 == 0) G = g;
@@ -527,8 +542,8 @@ int make_lane_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, 
 // CBP_PLAN_FP=0 keeps the lane-parallel plan, CBP_PLAN_LEVEL=0 skips the wavefront kernel.
 int make_plan(const cbp_code* c, const DeviceInfo& di, int alg, int batch, Plan* out,
               int stop = CBP_STOP_SYNDROME, bool allow_fp = true) {
-  if ((alg == ALG_LBP_NMS || alg == ALG_CBP_NMS) && allow_fp) {  // the same choice, no
-                                                                // frame-parallel kernel
+  if ((alg == ALG_LBP_NMS || alg == ALG_CBP_NMS || alg == ALG_FBP_SP) && allow_fp) {
+    // the same choice for the comparators, which have no frame-parallel kernel
     const char* el = std::getenv("CBP_PLAN_LEVEL");
     if (el && el[0] == '1') return make_level_plan(c, di, batch, out, alg);
     const int rc = make_lane_plan(c, di, alg, batch, out, stop);
@@ -608,6 +623,8 @@ KParams code_params(const cbp_code* c, const DeviceInfo& di, const Plan& pl, int
   p.lvl_edge = c->d.lvl_edge;
   p.lvl_rec8 = c->d.lvl_rec8;
   p.last_chk = c->d.last_chk;
+  p.lvl_cptr = c->d.lvl_cptr;
+  p.lvl_cedge = c->d.lvl_cedge;
   p.nlev = c->nlev;
   p.lvl_lanes = pl.lvl_lanes;
   p.lvl_test = c->lvl_test;
@@ -708,11 +725,20 @@ int build_level_tables(cbp_code* c, const std::vector<BaseEdge>& edges,
   }
   std::vector<int> lastc(N);
   for (int v = 0; v < N; ++v) lastc[v] = cpos[echk[last_e[v]]];
+  std::vector<int> cptr(N + 1, 0), cedge(E);  // each variable's edges, ascending check
+  for (int e = 0; e < E; ++e) ++cptr[ev[e] + 1];
+  for (int v = 0; v < N; ++v) cptr[v + 1] += cptr[v];
+  {
+    std::vector<int> fill(cptr.begin(), cptr.end() - 1);
+    for (int e = 0; e < E; ++e) cedge[fill[ev[e]]++] = newidx[e];  // e ascends with the check
+  }
   bool ok = cudaMalloc(&c->d.lvl_ptr, sizeof(int) * lptr.size()) == cudaSuccess &&
             cudaMalloc(&c->d.lvl_e0, sizeof(int) * e0.size()) == cudaSuccess &&
             cudaMalloc(&c->d.lvl_edge, sizeof(LvlEdge) * rec.size()) == cudaSuccess &&
             (!small || cudaMalloc(&c->d.lvl_rec8, sizeof(uint2) * rec8.size()) == cudaSuccess) &&
-            cudaMalloc(&c->d.last_chk, sizeof(int) * lastc.size()) == cudaSuccess;
+            cudaMalloc(&c->d.last_chk, sizeof(int) * lastc.size()) == cudaSuccess &&
+            cudaMalloc(&c->d.lvl_cptr, sizeof(int) * cptr.size()) == cudaSuccess &&
+            cudaMalloc(&c->d.lvl_cedge, sizeof(int) * cedge.size()) == cudaSuccess;
   if (!ok) return CBP_ENOMEM;
   ok = cudaMemcpy(c->d.lvl_ptr, lptr.data(), sizeof(int) * lptr.size(),
                   cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -723,6 +749,10 @@ int build_level_tables(cbp_code* c, const std::vector<BaseEdge>& edges,
        (!small || cudaMemcpy(c->d.lvl_rec8, rec8.data(), sizeof(uint2) * rec8.size(),
                              cudaMemcpyHostToDevice) == cudaSuccess) &&
        cudaMemcpy(c->d.last_chk, lastc.data(), sizeof(int) * lastc.size(),
+                  cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(c->d.lvl_cptr, cptr.data(), sizeof(int) * cptr.size(),
+                  cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(c->d.lvl_cedge, cedge.data(), sizeof(int) * cedge.size(),
                   cudaMemcpyHostToDevice) == cudaSuccess;
   if (!ok) return CBP_ECUDA;
   c->nlev = nlev;
@@ -892,6 +922,8 @@ void cbp_code_destroy(cbp_code_t* c) {
   cudaFree(c->d.lvl_edge);
   cudaFree(c->d.lvl_rec8);
   cudaFree(c->d.last_chk);
+  cudaFree(c->d.lvl_cptr);
+  cudaFree(c->d.lvl_cedge);
   delete c;
 }
 

@@ -124,6 +124,8 @@ struct CodeDev {
   LvlEdge* lvl_edge = nullptr;  // [E]
   uint2* lvl_rec8 = nullptr;   // [E] 8-byte records (M <= 4096, E < 2^20), else null
   int* last_chk = nullptr;     // [N] the last check of each variable (level order)
+  int* lvl_cptr = nullptr;     // [N + 1] each variable's edges ...
+  int* lvl_cedge = nullptr;    // [E] ... by level-ordered index, ascending check index
   BaseEdge* edges = nullptr;  // [nnzb]
   SpEdge* spe = nullptr;      // [nnzb], CBP-SP kernel records
   int* rptr = nullptr;        // [mb + 1]
@@ -171,6 +173,8 @@ struct KParams {
   const LvlEdge* lvl_edge;
   const uint2* lvl_rec8;
   const int* last_chk;
+  const int* lvl_cptr;
+  const int* lvl_cedge;
   int nlev, lvl_lanes;
   int lvl_test;           // the widest level (tested first at a sweep's end)
 };
@@ -206,6 +210,7 @@ struct Variant {
   bool rstore = false;     // CBP min-sum: C2V messages kept per edge (no rebuild)
   bool lvl = false;        // CBP-SP / min-sum on the wavefront schedule of the expanded graph
   bool shrec = false;      // that kernel with its edge records in shared memory
+  int deg = 0;             // wavefront flooding kernel: its degree bucket (8, 16 or 32)
 };
 
 // Sizes that fix the shared-memory and workspace layout of a launch.
@@ -230,6 +235,7 @@ void* sp_kernel_ptr(bool chk_shared, int fpt, bool wide, bool self_last);  // cb
 void* level_kernel_ptr(bool shrec);  // cbp_level.cu
 void* lbp_level_kernel_ptr(bool shv);
 void* nms_level_kernel_ptr(bool shrec);
+void* fbp_level_kernel_ptr(bool shv, int maxdeg);
 int level_max_threads();
 void* sp_multi_kernel_ptr(bool chk_shared, int fpt, bool self_last);  // cbp_sp.cu
 void* sp_win_kernel_ptr(bool chk_shared);                   // cbp_sp.cu

@@ -616,7 +616,151 @@ __global__ void __launch_bounds__(kLvlMaxThreads, 1) nms_level_kernel(const KPar
   }
 }
 
+// Flooding sum-product BP (Sec. II-A, Eqs. s3e1, s3e2, s2e6, s2e7), the comparator, with the
+// same lane groups: flooding has no order among checks, so the check phase takes the
+// level-ordered checks on the lanes, then the variable phase the variables.  Per group,
+// shared memory holds Lambda for every variable and the decision bits, the workspace the
+// C2V messages by level-ordered edge; SHV instances also copy each edge's variable index,
+// the check offsets and each variable's edges (ascending check index, the order of the
+// posterior's sum) into shared memory.  The arithmetic is the lane-parallel flooding
+// kernel's, operation for operation; a check's phi values stay in registers (D >= degree).
+template <bool SHV, int D>
+__global__ void __launch_bounds__(kLvlMaxThreads, 1) fbp_level_kernel(const KParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int G = p.lvl_lanes, F = p.F;
+  const int N = p.N, M = p.M, E = p.E, words = p.words;
+  const int tid = threadIdx.x;
+  const int g = tid / G, l = tid - g * G;
+  unsigned char* sp = smem;
+  float4* s_tab = reinterpret_cast<float4*>(sp);
+  sp += sizeof(float4) * kPhiSegments;
+  int* s_unsat = reinterpret_cast<int*>(sp);
+  sp += sizeof(int) * 16;
+  uint32_t* s_v = reinterpret_cast<uint32_t*>(sp);
+  int* s_e0 = reinterpret_cast<int*>(s_v + ((E + 3) & ~3));
+  int* s_cp = s_e0 + ((M + 1 + 3) & ~3);
+  int* s_ce = s_cp + ((N + 1 + 3) & ~3);
+  if (SHV)
+    sp += sizeof(int) * (2 * ((E + 3) & ~3) + ((M + 1 + 3) & ~3) + ((N + 1 + 3) & ~3));
+  for (int i = tid; i < kPhiSegments; i += blockDim.x) s_tab[i] = p.phi_tab[i];
+  if (tid < 16) s_unsat[tid] = 0;
+  if (SHV) {
+    for (int i = tid; i < E; i += blockDim.x) {
+      s_v[i] = p.lvl_edge[i].x & kSpMask;
+      s_ce[i] = p.lvl_cedge[i];
+    }
+    for (int i = tid; i <= M; i += blockDim.x) s_e0[i] = p.lvl_e0[i];
+    for (int i = tid; i <= N; i += blockDim.x) s_cp[i] = p.lvl_cptr[i];
+  }
+  __syncthreads();
+  if (g >= F) return;
+  const int* e0t = SHV ? s_e0 : p.lvl_e0;
+  const int* cpt = SHV ? s_cp : p.lvl_cptr;
+  const int* cet = SHV ? s_ce : p.lvl_cedge;
+  const LvlEdge* __restrict__ led = p.lvl_edge;
+  float* lam = reinterpret_cast<float*>(sp) + static_cast<size_t>(g) * p.sh_frame;
+  uint32_t* bits = reinterpret_cast<uint32_t*>(lam + ((N + 3) & ~3));
+  const long long slot = static_cast<long long>(blockIdx.x) * F + g;
+  float* R = p.ws + slot * p.ws_slot;
+  const float4* tab = s_tab;
+  const float xlo = p.phi_xlo;
+  const int bar_id = 1 + g;
+  auto var_of = [&](int e) -> int {
+    return SHV ? static_cast<int>(s_v[e]) : static_cast<int>(__ldg(&led[e].x) & kSpMask);
+  };
+
+  for (long long frame = slot; frame < p.batch; frame += p.slots) {
+    const float* L = p.llr + frame * N;
+    bool bad = false;
+    for (int v = l; v < N; v += G) {  // R = 0, so Lambda = L + 0 (Eq. s2e6)
+      lam[v] = __fadd_rn(__ldg(L + v), 0.0f);
+      bad |= non_finite(lam[v]);
+    }
+    if (bad) atomicOr(p.status, kStatusNonFiniteLlr);
+    team_sync(bar_id, G);
+
+    for (int t = 1;; ++t) {
+      // ---- every check: Eqs. (s3e1), (s3e2)
+      for (int ci = l; ci < M; ci += G) {
+        const int k0 = e0t[ci], d = e0t[ci + 1] - k0;
+        float ph[D];
+        uint32_t neg = 0, sig = 0;
+        float S = 0.0f;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          if (j < d) {
+            const float q = __fsub_rn(lam[var_of(k0 + j)], t > 1 ? R[k0 + j] : 0.0f);
+            const uint32_t n = q < 0.0f;
+            neg |= n << j;
+            sig ^= n;
+            ph[j] = phi_eval(fabsf(q), xlo, tab);
+            S = __fadd_rn(S, ph[j]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          if (j < d) {
+            const float mag = phi_eval(fabsf(__fsub_rn(S, ph[j])), xlo, tab);
+            R[k0 + j] = (sig ^ ((neg >> j) & 1u)) ? -mag : mag;
+          }
+        }
+      }
+      team_sync(bar_id, G);
+      // ---- posterior, Eq. (s2e6), in ascending check order; decisions, Eq. (s2e7)
+      for (int vb = 0; vb < N; vb += G) {
+        const int v = vb + l;
+        bool ng = false;
+        if (v < N) {
+          float s = __ldg(L + v);
+          const int c1 = cpt[v + 1];
+          for (int k = cpt[v]; k < c1; ++k) s = __fadd_rn(s, R[cet[k]]);
+          lam[v] = s;
+          ng = s < 0.0f;
+          if (p.soft) p.soft[frame * N + v] = s;
+        }
+        const unsigned wv = __ballot_sync(0xffffffffu, ng);
+        if ((l & 31) == 0 && v < N) bits[v >> 5] = wv;
+      }
+      team_sync(bar_id, G);
+      bool fail = false;
+      for (int ci = l; ci < M; ci += G) {
+        uint32_t par = 0;
+        const int e1 = e0t[ci + 1];
+        for (int e = e0t[ci]; e < e1; ++e) {
+          const uint32_t v = static_cast<uint32_t>(var_of(e));
+          par ^= bits[v >> 5] >> (v & 31);
+        }
+        fail |= (par & 1u) != 0;
+      }
+      if (fail) s_unsat[g] = 1;
+      team_sync(bar_id, G);
+      const bool ok = *static_cast<volatile int*>(&s_unsat[g]) == 0;
+      const bool done = (ok && p.stop == CBP_STOP_SYNDROME) || t >= p.max_iter;
+      if (done) {
+        uint32_t* ho = p.hard + frame * words;
+        for (int w = l; w < words; w += G) ho[w] = bits[w];
+        if (l == 0) p.iters[frame] = ok ? t : -t;
+      }
+      team_sync(bar_id, G);
+      if (l == 0) s_unsat[g] = 0;
+      team_sync(bar_id, G);
+      if (done) break;
+    }
+  }
+}
+
 }  // namespace
+
+void* fbp_level_kernel_ptr(bool shv, int maxdeg) {
+  if (maxdeg <= 8)
+    return shv ? reinterpret_cast<void*>(&fbp_level_kernel<true, 8>)
+               : reinterpret_cast<void*>(&fbp_level_kernel<false, 8>);
+  if (maxdeg <= 16)
+    return shv ? reinterpret_cast<void*>(&fbp_level_kernel<true, 16>)
+               : reinterpret_cast<void*>(&fbp_level_kernel<false, 16>);
+  return shv ? reinterpret_cast<void*>(&fbp_level_kernel<true, kMaxDeg>)
+             : reinterpret_cast<void*>(&fbp_level_kernel<false, kMaxDeg>);
+}
 
 void* nms_level_kernel_ptr(bool shrec) {
   return shrec ? reinterpret_cast<void*>(&nms_level_kernel<true>)

@@ -562,12 +562,13 @@ LBP_LEVEL_CASES = [("peg", 700, 2.0, 0.75, 96, "1"), ("peg", 300, 1.75, 1.0, 64,
                    ("2304", 100, 2.0, 1.0, 64, "1")]
 
 
-@pytest.mark.parametrize("alg", ["lbp_nms", "cbp_nms"])
+@pytest.mark.parametrize("alg", ["lbp_nms", "cbp_nms", "fbp_sp"])
 @pytest.mark.parametrize("name,batch,ebn0,alpha,lanes,shv", LBP_LEVEL_CASES)
-def test_level_schedule_min_sum(monkeypatch, alg, name, batch, ebn0, alpha, lanes, shv):
-    # Layered min-sum and CBP min-sum on the same wavefront schedule: the planner's choice for
-    # the Z = 1 PEG codes, forced elsewhere; normalisations, lane groups, edge records in
-    # shared or global memory, soft output: bit for bit against the oracle.
+def test_level_schedule_comparators(monkeypatch, alg, name, batch, ebn0, alpha, lanes, shv):
+    # Layered min-sum, CBP min-sum (both on the wavefront schedule) and flooding BP (all
+    # checks at once) with lane groups per frame: the planner's choice for the Z = 1 PEG
+    # codes, forced elsewhere; normalisations, lane groups, edge tables in shared or global
+    # memory, soft output: bit for bit against the oracle.
     qc = {"576": I.code_576, "2304": I.code_2304, "peg": I.code_peg_2048,
           "pegirr": I.code_peg_irregular_2048,
           "z4": lambda: I.relift(I.code_576(), 4)}[name]()
