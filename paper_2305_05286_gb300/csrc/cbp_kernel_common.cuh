@@ -23,6 +23,16 @@ __device__ __forceinline__ void warp_or_bit(uint32_t* word, uint32_t bit, bool a
   if ((threadIdx.x & 31) == __ffs(grp) - 1 && val) atomicOr(word, val);
 }
 
+// Bulk prefetch of [a, b) into L2, shrunk to whole 16-byte units inside the range.
+__device__ __forceinline__ void prefetch_l2(const float* a, const float* b) {
+  const uintptr_t lo = (reinterpret_cast<uintptr_t>(a) + 15) & ~uintptr_t(15);
+  const uintptr_t hi = reinterpret_cast<uintptr_t>(b) & ~uintptr_t(15);
+  if (hi > lo)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo),
+                 "r"(static_cast<uint32_t>(hi - lo))
+                 : "memory");
+}
+
 // Barrier over one team of lane groups (named barrier `id`, `n` threads; id 0 with
 // n = blockDim.x is the whole CTA).  Teams run their sweeps independently, so one
 // team's memory waits overlap another team's arithmetic.

@@ -162,14 +162,30 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
     if (act && my->t == 0) {  // Q*_v = L_v (CBP, Eq. s4e15); Lambda_v = L_v (LBP)
       const float* src = p.llr + static_cast<long long>(frame) * N;
       bool bad = false;
-      for (int c = 0; c < p.nb; ++c) {
-        const uint2 ci = s_col[c];
-        const int idx = ci.y & 0xffff;
-        const float L =
-            __ldg(src + c * Z + ((ci.y & 0x10000u) ? mod_add(z + int(ci.x >> 16), Z) : z));
-        bad |= non_finite(L);
-        if (ci.y & 0x10000u) SV[idx * Z + z] = L;
-        else VAR[idx * Z + z] = L;
+      constexpr int LB = 4;  // the loads of a block of columns are issued together
+      for (int c0 = 0; c0 < p.nb; c0 += LB) {
+        float Lb[LB];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+          const int c = c0 + u;
+          if (c < p.nb) {
+            const uint2 ci = s_col[c];
+            Lb[u] = __ldg(src + c * Z +
+                          ((ci.y & 0x10000u) ? mod_add(z + int(ci.x >> 16), Z) : z));
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+          const int c = c0 + u;
+          if (c < p.nb) {
+            const uint2 ci = s_col[c];
+            const int idx = ci.y & 0xffff;
+            const float L = Lb[u];
+            bad |= non_finite(L);
+            if (ci.y & 0x10000u) SV[idx * Z + z] = L;
+            else VAR[idx * Z + z] = L;
+          }
+        }
       }
       if (bad) atomicOr(p.status, kStatusNonFiniteLlr);
     }
@@ -178,6 +194,20 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
 
     for (int r = 0; r < p.mb; ++r) {
       if (act) {
+        if (!RST && t > 1 && z == 0) {
+          // the check states of base row r + 1 (cyclically) are contiguous in the
+          // workspace: one bulk L2 prefetch per lane group brings them on chip while this
+          // row runs (a non-binding hint), and the state block of that row's weight-1
+          // column when it ends the row
+          const int rn = r + 1 < p.mb ? r + 1 : 0;
+          const float* a = reinterpret_cast<const float*>(AUX + rn * Z);
+          prefetch_l2(a, a + 4 * Z);
+          const BaseEdge bl = s_e[s_rptr[rn + 1] - 1];
+          if (bl.flags & kSelf) {
+            const float* sv = SV + (bl.pad & 0xffff) * Z;
+            prefetch_l2(sv, sv + Z);
+          }
+        }
         const int k0 = s_rptr[r], d = s_rptr[r + 1] - k0;
         const int m = r * Z + z;
         if (CBP) {
@@ -313,40 +343,62 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
     const bool full =
         act && (t >= p.max_iter || (p.stop == CBP_STOP_SYNDROME &&
                                     *static_cast<volatile int*>(&my->unsat) == 0));
+    // a frame tested in full most likely stops now: ask L2 for the channel LLRs of its
+    // slot's next frame while the flush and the syndrome scan run
+    if (full && z == 0 && frame + p.slots < p.batch) {
+      const float* nx = p.llr + static_cast<long long>(frame + p.slots) * N;
+      for (int o = 0; o < N; o += 8192) prefetch_l2(nx + o, nx + min(o + 8192, N));
+    }
     // the decision bits are zero here (cleared at the start and after each full test);
     // the warp skips the flush when none of its frames needs it
     if (__any_sync(0xffffffffu, full)) {
-      for (int c = 0; c < p.nb; ++c) {
-        const uint2 ci = s_col[c];
-        const int cidx = ci.y & 0xffff;
-        const int sk = int(ci.x >> 16), rk = int(ci.x & 0xffff);
-        int v = 0;
-        bool neg = false;
-        if (full) {
-          float q;
-          int ck;
-          if (ci.y & 0x10000u) {  // weight-1 column: lane z owns its single check (rk, z)
-            q = SV[cidx * Z + z];
-            ck = rk * Z + z;
-            v = c * Z + mod_add(z + sk, Z);
-          } else {
-            q = VAR[cidx * Z + z];
-            int zk = z - sk;
-            zk = zk < 0 ? zk + Z : zk;
-            ck = rk * Z + zk;
-            v = c * Z + z;
+      constexpr int FC = 2;  // columns per block: the block's loads are issued together
+      for (int c0 = 0; c0 < p.nb; c0 += FC) {
+        float qb[FC];
+        float2 pcb[FC];
+        int vb[FC];
+#pragma unroll
+        for (int u = 0; u < FC; ++u) {
+          const int c = c0 + u;
+          vb[u] = 0;
+          if (full && c < p.nb) {
+            const uint2 ci = s_col[c];
+            const int cidx = ci.y & 0xffff;
+            const int sk = int(ci.x >> 16), rk = int(ci.x & 0xffff);
+            int ck;
+            if (ci.y & 0x10000u) {  // weight-1 column: lane z owns its single check (rk, z)
+              qb[u] = SV[cidx * Z + z];
+              ck = rk * Z + z;
+              vb[u] = c * Z + mod_add(z + sk, Z);
+            } else {
+              qb[u] = VAR[cidx * Z + z];
+              int zk = z - sk;
+              zk = zk < 0 ? zk + Z : zk;
+              ck = rk * Z + zk;
+              vb[u] = c * Z + z;
+            }
+            if (CBP) pcb[u] = CHK[ck];
           }
-          float lb = q;
-          if (CBP) {  // flushed posterior: Eq. (s4e20) with the last check of v as c_j
-            const float2 pc = CHK[ck];
-            const float b1 = fabsf(pc.x);
-            const float rm = __fmul_rn(alpha, (fabsf(q) == b1) ? pc.y : b1);
-            lb = __fadd_rn(q, (sign_bit(pc.x) ^ (q < 0.0f)) ? -rm : rm);
-          }
-          neg = lb < 0.0f;
-          if (p.soft) p.soft[static_cast<long long>(frame) * N + v] = lb;
         }
-        warp_or_bit(bits + (v >> 5), neg ? (1u << (v & 31)) : 0u, full);
+#pragma unroll
+        for (int u = 0; u < FC; ++u) {
+          if (c0 + u >= p.nb) break;  // uniform across the warp
+          const int v = vb[u];
+          bool neg = false;
+          if (full) {
+            const float q = qb[u];
+            float lb = q;
+            if (CBP) {  // flushed posterior: Eq. (s4e20) with the last check of v as c_j
+              const float2 pc = pcb[u];
+              const float b1 = fabsf(pc.x);
+              const float rm = __fmul_rn(alpha, (fabsf(q) == b1) ? pc.y : b1);
+              lb = __fadd_rn(q, (sign_bit(pc.x) ^ (q < 0.0f)) ? -rm : rm);
+            }
+            neg = lb < 0.0f;
+            if (p.soft) p.soft[static_cast<long long>(frame) * N + v] = lb;
+          }
+          warp_or_bit(bits + (v >> 5), neg ? (1u << (v & 31)) : 0u, full);
+        }
       }
     }
     team_sync(bar_id, bar_n);

@@ -231,16 +231,6 @@ __device__ __forceinline__ void row_edges(int k0, int k1, const SpEdge* __restri
 
 constexpr int kPrefetchRows = 1;
 
-// Bulk prefetch of [a, b) into L2, shrunk to whole 16-byte units inside the range.
-__device__ __forceinline__ void prefetch_l2(const float* a, const float* b) {
-  const uintptr_t lo = (reinterpret_cast<uintptr_t>(a) + 15) & ~uintptr_t(15);
-  const uintptr_t hi = reinterpret_cast<uintptr_t>(b) & ~uintptr_t(15);
-  if (hi > lo)
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo),
-                 "r"(static_cast<uint32_t>(hi - lo))
-                 : "memory");
-}
-
 // Paper-literal stop: one thread of a lane group walks the row's check updates in order
 // (lane z = check r*Z + z) with the window counter wst[0]; wst[1] receives the lane at
 // which the counter reaches M, or -1.  ok[z] = 1 if check z left Omega > 0 and flipped
