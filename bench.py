@@ -576,11 +576,17 @@ def run_learned(args):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         ev[0].record(stream)
         # checkpoint spacing T: the forward records the tape, the backward recomputes nothing
-        soft = cbp.weighted_cbp(code, llr, w, T, T)
+        # --norm-weights: each sweep's scales divided by their mean, so training can
+        # reweight the base rows of a sweep against each other but not inflate a sweep
+        weff = w / w.mean(dim=1, keepdim=True) if args.norm_weights else w
+        soft = cbp.weighted_cbp(code, llr, weff, T, T)
         if args.loss == "bce":
             loss = torch.nn.functional.binary_cross_entropy_with_logits(-soft, cw.float())
-        else:  # soft bit-error rate: mean sigmoid of the margin by which a bit is wrong
+        elif args.loss == "soft_ber":  # mean sigmoid of the margin by which a bit is wrong
             loss = torch.sigmoid(soft * (2.0 * cw.float() - 1.0)).mean()
+        else:  # soft frame-error rate: 1 - prod over the bits of sigmoid(-margin), per frame
+            m = soft * (2.0 * cw.float() - 1.0)
+            loss = (1.0 - torch.exp(-torch.nn.functional.softplus(m).sum(dim=1))).mean()
         opt.zero_grad(set_to_none=True)
         ev[1].record(stream)
         loss.backward()
@@ -598,7 +604,7 @@ def run_learned(args):
     step_ms = {"forward_loss": med([a.elapsed_time(b) for a, b, _ in step_ev]),
                "backward": med([b.elapsed_time(c) for _, b, c in step_ev]),
                "steps_timed": len(step_ev)}
-    wl = w.detach().clone()
+    wl = (w / w.mean(dim=1, keepdim=True) if args.norm_weights else w).detach().clone()
     ones = torch.ones_like(wl)
     rows = []
     chunk = min(args.eval_frames, 16384)
@@ -637,6 +643,7 @@ def run_learned(args):
     print(json.dumps({"code": args.learned_code, "zero_codeword": zero,
                       "learned_weights": wl.cpu().numpy().round(4).tolist(),
                       "train_steps": args.train_steps, "train_frames": B, "loss": args.loss,
+                      "norm_weights": bool(args.norm_weights),
                       "lr": args.lr,
                       "train_seconds": train_s, "train_step_ms_median": step_ms,
                       "loss_first_last": [losses[0], losses[-1]]}),
@@ -860,9 +867,13 @@ def main():
     ap.add_argument("--train-frames", type=int, default=8192)
     ap.add_argument("--eval-frames", type=int, default=1_000_000)
     ap.add_argument("--lr", type=float, default=0.01)
-    ap.add_argument("--loss", default="bce", choices=["bce", "soft_ber"],
-                    help="learned weights: mean BCE of the output LLRs, or the mean sigmoid of "
-                         "each bit's wrong-side margin (a smooth bit-error rate)")
+    ap.add_argument("--loss", default="bce", choices=["bce", "soft_ber", "soft_fer"],
+                    help="learned weights: mean BCE of the output LLRs, the mean sigmoid of "
+                         "each bit's wrong-side margin (a smooth bit-error rate), or one minus "
+                         "the product of the bits' sigmoid(-margin) per frame (a smooth "
+                         "frame-error rate)")
+    ap.add_argument("--norm-weights", action="store_true",
+                    help="learned weights: each sweep's base-row scales normalised to mean 1")
     ap.add_argument("--sweep-lo", type=float, default=0.0)
     ap.add_argument("--sweep-hi", type=float, default=2.0)
     ap.add_argument("--no-comparators", action="store_true")
