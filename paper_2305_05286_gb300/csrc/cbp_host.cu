@@ -346,7 +346,7 @@ int make_fp_plan(const cbp_code* c, const DeviceInfo& di, int batch, Plan* out) 
 }
 
 // Launch plan of the wavefront-schedule kernel, one CTA per SM: as many lane groups (one
-// frame each) as shared memory holds (a frame's Q*/phi, check-beliefs and decision bits;
+// frame each) as shared memory holds (CBP-SP: a frame's Q*, check-beliefs and decision bits;
 // at most 15, one named barrier each), then the widest group of whole warps that keeps
 // the CTA within its thread limit, but no wider than the widest level (CBP_LVL_LANES =
 // 32..256 in the environment for tuning); fewer groups for small batches.  The workspace
@@ -369,7 +369,7 @@ int make_level_plan(const cbp_code* c, const DeviceInfo& di, int batch, Plan* ou
   const size_t fr_floats = lbp   ? 4 * static_cast<size_t>(c->M) + align4(c->N) + W
                            : nms ? 2 * static_cast<size_t>(c->M) + align4(c->N) + W
                            : fbp ? align4(c->N) + W
-                                 : 2 * static_cast<size_t>(c->N) + align4(c->M) + W;
+                                 : align4(c->N) + align4(c->M) + W;
   const size_t avail = static_cast<size_t>(di.smem_optin);
   const size_t recb = fbp ? sizeof(int) * (2 * align4(c->E) + align4(c->M + 1) + align4(c->N + 1))
                           : (lbp ? sizeof(uint32_t) * align4(c->E) : sizeof(uint2) * c->E) +

@@ -16,7 +16,8 @@
 // time.  Lane l takes the checks l, l + G, ... of a level; a named barrier over the group
 // ends the level.  Checks are numbered in level order (ci).  Per group, shared memory
 // holds the frame's state:
-//   QP   (Q*_v, phi(|Q*_v|)) for every variable                     [N]
+//   Q    Q*_v for every variable (phi(|Q*_v|) is evaluated where it is read: keeping only
+//        Q* leaves room for more frames per SM)                       [N]
 //   S    check-beliefs, sign bit = sgn Omega, by level-ordered check  [M]
 //   bits decisions of the flushed posterior                          [words]
 // and the workspace the C2V messages R, indexed by the level-ordered edge, so the own
@@ -87,8 +88,8 @@ __global__ void __launch_bounds__(kLvlMaxThreads, 1) cbp_level_kernel(const KPar
   const int* e0t = SHREC ? s_e0 : p.lvl_e0;
   const LvlEdge* __restrict__ led = p.lvl_edge;
   float* gb = reinterpret_cast<float*>(sp) + static_cast<size_t>(g) * p.sh_frame;
-  float2* QP = reinterpret_cast<float2*>(gb);
-  float* S = gb + 2 * static_cast<size_t>(N);
+  float* Qv = gb;
+  float* S = gb + ((N + 3) & ~3);
   uint32_t* bits = reinterpret_cast<uint32_t*>(S + ((M + 3) & ~3));
   const long long slot = static_cast<long long>(blockIdx.x) * F + g;
   float* R = p.ws + slot * p.ws_slot;
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(kLvlMaxThreads, 1) cbp_level_kernel(const KPar
     for (int v = l; v < N; v += G) {
       const float L = __fadd_rn(__ldg(src + v), 0.0f);
       bad |= non_finite(L);
-      QP[v].x = L;
+      Qv[v] = L;
     }
     if (bad) atomicOr(p.status, kStatusNonFiniteLlr);
     team_sync(bar_id, G);
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(kLvlMaxThreads, 1) cbp_level_kernel(const KPar
           float Sacc = 0.0f;
           uint32_t sig = 0;
           for (int eb = e0t[ci]; eb < e1; eb += kLvlChunk) {
-            float q[kLvlChunk], ph[kLvlChunk], sj[kLvlChunk], ro[kLvlChunk];
+            float q[kLvlChunk], sj[kLvlChunk], ro[kLvlChunk];
             uint32_t vx[kLvlChunk];
             int pe[kLvlChunk];
 #pragma unroll
@@ -127,9 +128,7 @@ __global__ void __launch_bounds__(kLvlMaxThreads, 1) cbp_level_kernel(const KPar
                 const LvlRec rec = lvl_rec<SHREC>(s_rec, led, e);
                 vx[j] = rec.vx;
                 pe[j] = rec.pe;
-                const float2 qp = QP[rec.vx & kSpMask];
-                q[j] = qp.x;
-                ph[j] = qp.y;
+                q[j] = Qv[rec.vx & kSpMask];
                 sj[j] = S[rec.cj];
                 ro[j] = (!(rec.vx & kSpSelf) && t > 1) ? R[e] : 0.0f;
               }
@@ -139,7 +138,9 @@ __global__ void __launch_bounds__(kLvlMaxThreads, 1) cbp_level_kernel(const KPar
               if (eb + j < e1) {
                 const bool self = vx[j] & kSpSelf;
                 // B2V, Eqs. (s4e18), (s4e13); a variable not visited before adds no C2V
-                const float mag = phi_eval(fabsf(__fsub_rn(fabsf(sj[j]), ph[j])), xlo, tab);
+                // phi(|Q*_v|) of Eq. (s4e18), the value C2B stored with Q*_v
+                const float phq = phi_eval(fabsf(q[j]), xlo, tab);
+                const float mag = phi_eval(fabsf(__fsub_rn(fabsf(sj[j]), phq)), xlo, tab);
                 const float rb = __uint_as_float(
                     __float_as_uint(mag) |
                     ((__float_as_uint(sj[j]) ^ __float_as_uint(q[j])) & 0x80000000u));
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(kLvlMaxThreads, 1) cbp_level_kernel(const KPar
                 Sacc = __fadd_rn(Sacc, phn);
                 sig ^= __float_as_uint(qn);
                 if (!self && !first) R[pe[j]] = Rn;  // R_{c_j->v} <- R^new, Eq. (s4e22)
-                QP[vx[j] & kSpMask] = make_float2(qn, phn);
+                Qv[vx[j] & kSpMask] = qn;
               }
             }
           }
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(kLvlMaxThreads, 1) cbp_level_kernel(const KPar
           const int e1 = e0t[ci + 1];
           for (int e = e0t[ci]; e < e1; ++e) {
             const int v = static_cast<int>(lvl_rec<SHREC>(s_rec, led, e).vx & kSpMask);
-            const float2 qp = QP[v];
+            const float2 qp = make_float2(Qv[v], phi_eval(fabsf(Qv[v]), xlo, tab));
             const float Sk = S[__ldg(p.last_chk + v)];
             const float mag = phi_eval(fabsf(__fsub_rn(fabsf(Sk), qp.y)), xlo, tab);
             const float lb = __fadd_rn(
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(kLvlMaxThreads, 1) cbp_level_kernel(const KPar
         const int v = vb + l;
         bool neg = false;
         if (v < N) {
-          const float2 qp = QP[v];
+          const float2 qp = make_float2(Qv[v], phi_eval(fabsf(Qv[v]), xlo, tab));
           const float Sk = S[__ldg(p.last_chk + v)];
           const float mag = phi_eval(fabsf(__fsub_rn(fabsf(Sk), qp.y)), xlo, tab);
           const float lb = __fadd_rn(
