@@ -634,3 +634,60 @@ def test_frame_parallel_host_decode_and_status(monkeypatch):
     code.decode(torch.from_numpy(bad).cuda(), max_iter=5)
     torch.cuda.synchronize()
     assert code.device_status() == cbp.STATUS_NONFINITE_LLR
+
+
+def special_llrs(rng, B, N, ebn0_llr, cw):
+    """Channel LLRs with the values that exercise the edges of the arithmetic: +0 and -0,
+    subnormals, values just inside and outside the phi clamp (X_LO, 2 where phi changes
+    regime, 30), large finite magnitudes up to the largest float, mixed into ordinary
+    LLRs so that the frames still decode."""
+    x = ebn0_llr.copy()
+    xlo = np.float32(O.xlo32())
+    specials = np.array([0.0, -0.0, 1e-40, -1e-40, 1e-20, -1e-20, xlo, -xlo,
+                         np.nextafter(xlo, np.float32(0)), 2.0, -2.0,
+                         np.nextafter(np.float32(2.0), np.float32(0)), 30.0, -30.0,
+                         np.nextafter(np.float32(30.0), np.float32(100)), 1e6, -1e6,
+                         3.0e38, -3.0e38, np.finfo(np.float32).max, -np.finfo(np.float32).max],
+                        np.float32)
+    for b in range(B):
+        pos = rng.choice(N, size=N // 8, replace=False)
+        v = rng.choice(specials, size=pos.size)
+        if b % 2 == 0:  # even frames: each value takes the sign of its transmitted bit
+            # (BPSK: bit 1 is negative), so they still decode; odd frames keep random signs
+            v = np.where(cw[b, pos] != 0, -np.abs(v), np.abs(v)).astype(np.float32)
+        x[b, pos] = v
+    x[0, :] = 0.0          # a frame of erasures: every message starts from a zero
+    x[1, :] = -0.0
+    return x
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_special_llr_values(code576, large, alg):
+    """Frames full of signed zeros, subnormals, clamp-boundary and huge finite LLRs: every
+    decoder bit for bit against the oracle (hard decisions, iteration counts, soft
+    outputs), on the lane-parallel kernels of the 576- and 26112-bit codes."""
+    rng = np.random.default_rng(77)
+    qc, code, oc = code576
+    fr = I.make_frames(qc, 64, 2.0, seed=7700)
+    x = special_llrs(rng, 64, qc.N, fr.llr, fr.codewords)
+    ref = oc.decode(x, alg=alg, max_iter=30, threads=THREADS)
+    assert_parity(run_gpu(code, x, alg), ref, f"{alg} special 576")
+    qc, code, oc = large
+    llr, cw = I.make_frames_torch(qc, 24, 2.5, seed=7701)
+    x = special_llrs(rng, 24, qc.N, llr.cpu().numpy(), cw.cpu().numpy())
+    ref = oc.decode(x, alg=alg, max_iter=20, threads=THREADS)
+    assert_parity(run_gpu(code, x, alg, max_iter=20), ref, f"{alg} special 26112")
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_special_llr_values_wavefront(alg):
+    """The same frames through the wavefront-schedule kernels (the planner's choice for
+    the Z = 1 PEG code)."""
+    rng = np.random.default_rng(78)
+    qc = I.code_peg_2048()
+    code = cbp.Code.from_qc(qc)
+    assert code.launch_info(64, alg=alg)["level_schedule"] == 1
+    fr = I.make_frames(qc, 64, 2.0, seed=7800)
+    x = special_llrs(rng, 64, qc.N, fr.llr, fr.codewords)
+    ref = O.OracleCode(qc.base, qc.Z).decode(x, alg=alg, max_iter=20, threads=THREADS)
+    assert_parity(run_gpu(code, x, alg, max_iter=20), ref, f"{alg} special peg")
