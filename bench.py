@@ -65,13 +65,13 @@ CAPTURES = {
                "thread_inst_per_edge_sweep": 92.1, "issue_active": 0.523,
                "warps_active_per_sm": 23.9},
     "lbp_nms": {"kernel": "minsum_kernel<2, 0, 768, 0>(KParams)", "date": "2026-12-04", "frames": 2432,
-               "sources": "85f5f949341816e8", "dram_bytes_per_frame_sweep": 514696,
-               "thread_inst_per_edge_sweep": 76.2, "issue_active": 0.63,
+               "sources": "11960eefc1b530b6", "dram_bytes_per_frame_sweep": 513578,
+               "thread_inst_per_edge_sweep": 76.2, "issue_active": 0.631,
                "warps_active_per_sm": 22.3},
     "cbp_nms": {"kernel": "minsum_kernel<1, 0, 768, 0>(KParams)", "date": "2026-12-04", "frames": 2432,
-               "sources": "85f5f949341816e8", "dram_bytes_per_frame_sweep": 846139,
-               "thread_inst_per_edge_sweep": 95.4, "issue_active": 0.616,
-               "warps_active_per_sm": 21.6},
+               "sources": "11960eefc1b530b6", "dram_bytes_per_frame_sweep": 849329,
+               "thread_inst_per_edge_sweep": 86.5, "issue_active": 0.576,
+               "warps_active_per_sm": 21.7},
     "fbp_sp": {"kernel": "flood_kernel(KParams)", "date": "2026-12-04", "frames": 2432,
                "sources": "d4fcbc323157bf8c", "dram_bytes_per_frame_sweep": 789273,
                "thread_inst_per_edge_sweep": 109.7, "issue_active": 0.321,

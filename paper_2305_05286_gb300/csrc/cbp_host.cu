@@ -177,8 +177,9 @@ size_t shared_fixed_bytes(const Variant& v, const Shape& s, int groups) {
       b += sizeof(float4) * kPhiSegments + sizeof(ColEntry) * ((s.nnzb + 1) & ~1) +
            sizeof(int) * align4(s.nb + 1);
       break;
-    default:  // min-sum kernels
-      b += sizeof(uint2) * ((s.nb + 1) & ~1);
+    default:  // min-sum kernels; CBP min-sum also the entries' per-lane form (SpEdge)
+      b += (v.alg == ALG_CBP_NMS ? sizeof(SpEdge) * s.nnzb : 0) +
+           sizeof(uint2) * ((s.nb + 1) & ~1);
   }
   return b;
 }

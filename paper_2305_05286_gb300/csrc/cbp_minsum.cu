@@ -26,6 +26,16 @@ namespace {
 
 constexpr float kInf = __builtin_huge_valf();
 
+// CBP min-sum: lane z's slots of base entry `se` (the CBP-SP kernel's records,
+// lane-independent parts precomputed): its variable's state (weight >= 2 columns: position (z + s) mod Z of the
+// column; weight 1: the check lane's own slot) and its predecessor check.
+__device__ __forceinline__ int var_slot(const SpEdge& se, int z, int Z) {
+  return static_cast<int>(se.x & kSpMask) + z - (z >= static_cast<int>(se.w & 0xffffu) ? Z : 0);
+}
+__device__ __forceinline__ int pred_off(const SpEdge& se, int z, int Z) {
+  return z - (z >= static_cast<int>(se.w >> 16) ? Z : 0);
+}
+
 // Layered NMS on one check (lane z, check m = r*Z + z, d <= D edges): pass 1 forms
 // Q = Lambda - R_old (Eq. s2e10) and the minima, pass 2 forms R_new and
 // Lambda = Q + R_new (Eq. s2e12).  The V2C messages of the row stay in registers.
@@ -107,6 +117,10 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
   unsigned char* sp = smem;
   BaseEdge* s_e = reinterpret_cast<BaseEdge*>(sp);
   sp += sizeof(BaseEdge) * p.nnzb;
+  // CBP min-sum: the per-entry lane records of the CBP-SP kernel (two slots per edge: the
+  // variable's and the predecessor check's; layered min-sum, with one, keeps the plain list)
+  SpEdge* s_spe = reinterpret_cast<SpEdge*>(sp);
+  if (CBP) sp += sizeof(SpEdge) * p.nnzb;
   int* s_rptr = reinterpret_cast<int*>(sp);
   sp += sizeof(int) * ((p.mb + 1 + 3) & ~3);
   uint2* s_col = reinterpret_cast<uint2*>(sp);  // (last row | shift << 16, idx | self << 16)
@@ -115,7 +129,10 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
   sp += sizeof(SlotState) * ((G + 3) & ~3);
   float* s_groups = reinterpret_cast<float*>(sp);
 
-  for (int i = tid; i < p.nnzb; i += blockDim.x) s_e[i] = p.edges[i];
+  for (int i = tid; i < p.nnzb; i += blockDim.x) {
+    s_e[i] = p.edges[i];
+    if (CBP) s_spe[i] = p.spe[i];
+  }
   for (int i = tid; i <= p.mb; i += blockDim.x) s_rptr[i] = p.rptr[i];
   for (int c = tid; c < p.nb; c += blockDim.x) {
     const ColEntry ce = p.cols[p.cptr[c + 1] - 1];
@@ -236,18 +253,15 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
             for (int u = 0; u < 4; ++u) {
               const int j = j0 + u;
               if (j < d) {
-                const BaseEdge be = s_e[k0 + j];
-                const int zv = mod_add(z + be.s, Z);
-                const int cidx = be.pad & 0xffff;
-                fl[u] = be.flags;
-                qoff[u] = (be.flags & kSelf) ? cidx * Z + z : cidx * Z + zv;
-                q[u] = (be.flags & kSelf) ? SV[qoff[u]] : VAR[qoff[u]];
-                int zj = zv - be.ps;
-                zj = zj < 0 ? zj + Z : zj;
-                pc[u] = CHK[be.pr * Z + zj];
+                const SpEdge se = s_spe[k0 + j];
+                const int pz = pred_off(se, z, Z);
+                fl[u] = se.x;
+                qoff[u] = var_slot(se, z, Z);
+                q[u] = (se.x & kSpSelf) ? SV[qoff[u]] : VAR[qoff[u]];
+                pc[u] = CHK[static_cast<int>(se.y) + pz];
                 if (RST) {  // own slot (c_i -> v), predecessor slot (c_j -> v)
-                  ro[u] = (t > 1 && !(be.flags & kSelf)) ? Rg[(k0 + j) * Z + z] : 0.0f;
-                  roff[u] = be.pe * Z + zj;
+                  ro[u] = (t > 1 && !(se.x & kSpSelf)) ? Rg[(k0 + j) * Z + z] : 0.0f;
+                  roff[u] = static_cast<int>(se.z) + pz;
                 }
               }
             }
@@ -257,17 +271,17 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
               if (j < d) {
                 // B2V, Eq. (s4e18xx): min2 of c_j when |Q*_v| is its min1
                 float Rn = 0.0f;
-                if (!(t == 1 && (fl[u] & kFirst))) {
+                if (!(t == 1 && (fl[u] & kSpFirst))) {
                   const float b1 = fabsf(pc[u].x);
                   const float rm = __fmul_rn(alpha, (fabsf(q[u]) == b1) ? pc[u].y : b1);
                   Rn = (sign_bit(pc[u].x) ^ (q[u] < 0.0f)) ? -rm : rm;
                 }
                 float rold = 0.0f;
-                if (fl[u] & kSelf) {
+                if (fl[u] & kSpSelf) {
                   rold = Rn;                                   // c_j == c_i
                 } else if (RST) {
                   rold = ro[u];
-                  if (!(t == 1 && (fl[u] & kFirst))) Rg[roff[u]] = Rn;  // Eq. (s4e22)
+                  if (!(t == 1 && (fl[u] & kSpFirst))) Rg[roff[u]] = Rn;  // Eq. (s4e22)
                 } else if (t > 1) {
                   const float rm = (static_cast<uint32_t>(j) == oidx) ? r2 : r1;
                   rold = (osig ^ static_cast<uint32_t>((osg >> j) & 1ull)) ? -rm : rm;
@@ -284,7 +298,7 @@ __global__ void __launch_bounds__(MAXT, 1) minsum_kernel(const KParams p) {
                 const uint32_t neg = qn < 0.0f;
                 sig ^= neg;
                 if (!RST) sg |= static_cast<unsigned long long>(neg) << j;
-                if (fl[u] & kSelf) SV[qoff[u]] = qn;
+                if (fl[u] & kSpSelf) SV[qoff[u]] = qn;
                 else VAR[qoff[u]] = qn;
               }
             }
