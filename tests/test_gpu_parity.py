@@ -691,3 +691,21 @@ def test_special_llr_values_wavefront(alg):
     x = special_llrs(rng, 64, qc.N, fr.llr, fr.codewords)
     ref = O.OracleCode(qc.base, qc.Z).decode(x, alg=alg, max_iter=20, threads=THREADS)
     assert_parity(run_gpu(code, x, alg, max_iter=20), ref, f"{alg} special peg")
+
+
+@pytest.mark.parametrize("alg", ["cbp_nms", "lbp_nms", "fbp_sp"])
+@pytest.mark.parametrize("pos", [0, 11])
+def test_comparators_with_weight1_column_not_last(pos, alg):
+    # The min-sum and flooding kernels take a weight-1 edge anywhere in its row (CBP
+    # min-sum reads its slots from the per-entry lane records): the permuted code of the
+    # test above, bit for bit against the oracle.
+    base = I.code_576().base
+    w1 = int(np.nonzero((base >= 0).sum(0) == 1)[0][0])
+    perm = [c for c in range(base.shape[1]) if c != w1]
+    perm.insert(pos, w1)
+    qc = I.QCCode(np.ascontiguousarray(base[:, perm]), 24)
+    code = cbp.Code.from_qc(qc)
+    fr = I.make_frames(qc, 300, 2.0, seed=4400 + pos)
+    ref = O.OracleCode(qc.base, qc.Z).decode(fr.llr, alg=alg, max_iter=25, threads=THREADS)
+    assert (ref["iters"] > 1).any()
+    assert_parity(run_gpu(code, fr.llr, alg, max_iter=25), ref, f"{alg}, weight-1 column at {pos}")
