@@ -358,3 +358,50 @@ def test_noiseless_posteriors_grow_until_saturation(c576, alg):
             assert np.all(mag >= prev - 1e-12), f"sweep {t}"
         prev = mag
     assert prev.min() > 3.0
+
+
+# ------------------------------------------------------- flooding schedule on a loopy code
+def textbook_flooding(rows, L, sweeps, layered=False):
+    """Flooding BP as the sum-product textbook writes it (Sec. II-A, Eqs. s3e1, s3e2,
+    s2e6): every check forms its V2C messages from the posteriors of the previous
+    iteration minus its own old message, its C2V messages by the tanh rule over the other
+    edges, and the posteriors are summed once all checks are done.  FP64, tanh form (the
+    oracle uses the phi form).  layered=True updates the posteriors after every check
+    instead: the schedule mistake this pin must tell apart."""
+    L = np.asarray(L, np.float64)
+    R = [np.zeros(len(vs)) for vs in rows]
+    lam = L.copy()
+    for _ in range(sweeps):
+        for m, vs in enumerate(rows):
+            q = lam[vs] - R[m]
+            th = np.tanh(q / 2.0)
+            new = np.empty(len(vs))
+            for k in range(len(vs)):
+                new[k] = 2.0 * np.arctanh(np.prod(np.delete(th, k)))
+            if layered:
+                lam[vs] = q + new
+            R[m] = new
+        if not layered:
+            lam = L.copy()
+            for m, vs in enumerate(rows):
+                np.add.at(lam, vs, R[m])
+    return lam
+
+
+@pytest.mark.parametrize("sweeps", [1, 2, 4])
+def test_fbp_equals_textbook_flooding_on_a_loopy_code(c576, sweeps):
+    # On a cycle-free graph every schedule reaches the same exact marginals, so the tree
+    # pins cannot see the schedule.  On the 576-bit code (girth 6 at least, many cycles)
+    # the oracle's FP64 flooding BP must equal the textbook flooding recursion, and a
+    # layered update would not.
+    code, oc = c576
+    rows = code.check_rows()
+    fr = I.make_frames(code, 6, 1.0, seed=1300 + sweeps)
+    r = oc.decode(fr.llr.astype(np.float64), alg="fbp_sp", precision=64, max_iter=sweeps,
+                  stop="none")
+    for f in range(fr.llr.shape[0]):
+        ref = textbook_flooding(rows, fr.llr[f], sweeps)
+        assert np.abs(r["soft"][f] - ref).max() < 1e-6
+        if sweeps > 1 or f == 0:  # the layered schedule differs after its first check
+            lay = textbook_flooding(rows, fr.llr[f], sweeps, layered=True)
+            assert np.abs(r["soft"][f] - lay).max() > 1e-2
