@@ -361,13 +361,13 @@ def test_noiseless_posteriors_grow_until_saturation(c576, alg):
 
 
 # ------------------------------------------------------- flooding schedule on a loopy code
-def textbook_flooding(rows, L, sweeps, layered=False):
-    """Flooding BP as the sum-product textbook writes it (Sec. II-A, Eqs. s3e1, s3e2,
-    s2e6): every check forms its V2C messages from the posteriors of the previous
-    iteration minus its own old message, its C2V messages by the tanh rule over the other
-    edges, and the posteriors are summed once all checks are done.  FP64, tanh form (the
-    oracle uses the phi form).  layered=True updates the posteriors after every check
-    instead: the schedule mistake this pin must tell apart."""
+def textbook_bp(rows, L, sweeps, layered=False):
+    """Sum-product BP as the textbook writes it (Sec. II, Eqs. s3e1, s3e2, s2e6), FP64, in
+    the tanh form (the oracle uses the phi form).  Flooding: every check forms its V2C
+    messages from the posteriors of the previous iteration minus its own old message, its
+    C2V messages by the tanh rule over the other edges, and the posteriors are summed once
+    all checks are done.  layered=True: the checks in ascending order, each updating its
+    variables' posteriors at once (layered BP, Sec. II-B)."""
     L = np.asarray(L, np.float64)
     R = [np.zeros(len(vs)) for vs in rows]
     lam = L.copy()
@@ -400,8 +400,24 @@ def test_fbp_equals_textbook_flooding_on_a_loopy_code(c576, sweeps):
     r = oc.decode(fr.llr.astype(np.float64), alg="fbp_sp", precision=64, max_iter=sweeps,
                   stop="none")
     for f in range(fr.llr.shape[0]):
-        ref = textbook_flooding(rows, fr.llr[f], sweeps)
+        ref = textbook_bp(rows, fr.llr[f], sweeps)
         assert np.abs(r["soft"][f] - ref).max() < 1e-6
         if sweeps > 1 or f == 0:  # the layered schedule differs after its first check
-            lay = textbook_flooding(rows, fr.llr[f], sweeps, layered=True)
+            lay = textbook_bp(rows, fr.llr[f], sweeps, layered=True)
             assert np.abs(r["soft"][f] - lay).max() > 1e-2
+
+
+@pytest.mark.parametrize("sweeps", [1, 2, 4])
+def test_cbp_flushed_posterior_equals_textbook_layered_bp(c576, sweeps):
+    # CBP's flushed posterior after t sweeps is the posterior of layered BP after t sweeps
+    # (Eqs. s4e9-s4e14: CBP defers each C2V message to the variable's next check).  The
+    # layered recursion written above in the textbook tanh form, FP64, on the loopy 576-bit
+    # code, against the oracle's CBP (S domain, phi form, deferred messages).
+    code, oc = c576
+    rows = code.check_rows()
+    fr = I.make_frames(code, 6, 1.0, seed=1400 + sweeps)
+    r = oc.decode(fr.llr.astype(np.float64), alg="cbp_sp", precision=64, max_iter=sweeps,
+                  stop="none")
+    for f in range(fr.llr.shape[0]):
+        ref = textbook_bp(rows, fr.llr[f], sweeps, layered=True)
+        assert np.abs(r["soft"][f] - ref).max() < 1e-6
